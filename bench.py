@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: guiding-centre particle-steps/s on GB300 (one JSON line on rank 0).
+
+Workload: the perturbed Parker wind on a 256x128x256 FP32 grid (eps = 0.1, 8 modes) with
+three ensembles of 10^6 electrons at 81 keV injected at r = 0.28 AU, 24 deg latitude,
+lambda = 0.1, 0.5 and 1.0 AU (the three runs batched in one context). A bench step is one
+gc_advance of PUSH_STEPS guiding-centre steps of every particle (dt = 0.5 s) with the
+snapshot tallies armed (every 100 steps) and the cell sort every 1000 steps. The FP32
+path (double-float accumulators) is the timed path; the plain FP64 path is measured on
+the same workload for comparison. Inputs (268 MB grid, ~520 MB particle state) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2403_06706_gb300 import synth  # noqa: E402
+
+LAUNCH = dict(block=128, steps_per_launch=1000, sort_every=1000)
+PUSH_STEPS = 1000
+TALLY = dict(cadence=100, n_mu=32, n_E=32, n_r=64, n_age=32, E_lo_keV=5.0, E_hi_keV=600.0,
+             r_lo_au=0.1, r_hi_au=2.5, age_max_s=86400.0, rwin_lo_au=0.9, rwin_hi_au=1.1,
+             age_young_s=1200.0)
+METRIC = "GC particle-steps/s on 1 GB300: plain FP64 vs FP32/neural-field at stated error"
+UNIT = "particle-steps/s"
+# Algorithmic FP32 work of one particle-step of the FP32 path: two field evaluations
+# (gather 236 + right-hand side 319 flop each) plus predictor, corrector, double-float
+# accumulation, free path and shell test (121 flop); FMA = 2 flop, sqrt / rcp / div /
+# atan2 / floor = 1 each.
+FLOP_PER_PSTEP = 2 * (236 + 319) + 121
+# FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one push launch of this workload (ncu, profiles/push_fp32_c2.md); None
+# until captured for the current kernel
+PUSH_TRAFFIC_BYTES = None
+SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def workload():
+    return synth.c2_perturbed()
+
+
+def config_dict(wl, n_per_rank):
+    return {
+        "workload": wl.name,
+        "grid": f"{wl.wind.n_r}x{wl.wind.n_th}x{wl.wind.n_ph}x8 f32, r {wl.wind.r_min_au}-{wl.wind.r_max_au} AU",
+        "perturbation": {"eps": wl.wind.eps, "modes": wl.wind.n_modes},
+        "particles_per_gpu": n_per_rank,
+        "lambda_au": [e.lam_au for e in wl.ensembles],
+        "energy_keV": 81.0,
+        "dt_s": wl.dt,
+        "push_steps_per_step": PUSH_STEPS,
+        "tally_cadence": TALLY["cadence"],
+        "sort_every": LAUNCH["sort_every"],
+        "l2": "inputs larger than L2 (268 MB grid, ~520 MB particle state per GPU); no flush",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples of one GPU while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             + ",".join("clocks_event_reasons." + r for r in SM_REASONS))
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 5 + len(SM_REASONS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(SM_REASONS, parts[5:5 + len(SM_REASONS)]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, nodes, seconds=10.0):
+    """The FP64 oracle as it stands, on the host cores: the first 4096 ids of every
+    ensemble of the workload, advanced from injection for about `seconds`."""
+    import oracle
+    from oracle import AU
+
+    f = oracle.grid_field(nodes, wl.wind.r_min_au * AU, wl.wind.r_max_au * AU)
+    p = oracle.params(seed=wl.seed)
+    oe = [oracle.ensemble(r0_au=e.r0_au, lat_deg=e.lat_deg, lon_deg=e.lon_deg, E0_keV=e.E0_keV,
+                          lam_au=e.lam_au, r_in_au=e.r_in, r_out_au=e.r_out_au) for e in wl.ensembles]
+    n_s = 4096
+    first = np.cumsum([0] + [e.count for e in wl.ensembles])[:-1]
+    parts = []
+    for k, f0 in enumerate(first):
+        counts = [0] * len(oe)
+        counts[k] = n_s
+        parts.append(oracle.inject(f, p, oe, counts, id0=int(f0), dt=wl.dt))
+    st = oracle.StateArrays({k: np.concatenate([q[k] for q in parts], axis=-1) for k in parts[0].arrays})
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.advance(f, p, oe, st, 0.0, 0, wl.dt, 50, n_threads=cores)
+    pilot = time.perf_counter() - t0
+    n_steps = int(max(50, min(40000, 50 * seconds / max(pilot, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.advance(f, p, oe, st, 50 * wl.dt, 50, wl.dt, n_steps, n_threads=cores)
+    el = time.perf_counter() - t0
+    return {"value": st.n * n_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{st.n} particles (first {n_s} ids of each lambda ensemble) x {n_steps} "
+                      f"steps after 50 from injection, FP64 oracle on the same FP32 grid values, "
+                      f"{el:.1f} s wall"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import AU
+
+    wl = workload()
+    nodes = synth.wind_grid(wl.wind, dtype=np.float32)
+    f = oracle.grid_field(nodes, wl.wind.r_min_au * AU, wl.wind.r_max_au * AU)
+    p = oracle.params(seed=wl.seed)
+    oe = [oracle.ensemble(r0_au=e.r0_au, lat_deg=e.lat_deg, lon_deg=e.lon_deg, E0_keV=e.E0_keV,
+                          lam_au=e.lam_au, r_in_au=e.r_in, r_out_au=e.r_out_au) for e in wl.ensembles]
+    n_s = 512
+    first = np.cumsum([0] + [e.count for e in wl.ensembles])[:-1]
+    parts = []
+    for k, f0 in enumerate(first):
+        counts = [0] * len(oe)
+        counts[k] = n_s
+        parts.append(oracle.inject(f, p, oe, counts, id0=int(f0), dt=wl.dt))
+    st = oracle.StateArrays({k: np.concatenate([q[k] for q in parts], axis=-1) for k in parts[0].arrays})
+    cores = os.cpu_count() or 1
+    ref_steps = 2000  # push steps per bench step of this arm
+    t, k = 0.0, 0
+    for _ in range(args.warmup):
+        oracle.advance(f, p, oe, st, t, k, wl.dt, ref_steps, n_threads=cores)
+        t += ref_steps * wl.dt
+        k += ref_steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.advance(f, p, oe, st, t, k, wl.dt, ref_steps, n_threads=cores)
+        t += ref_steps * wl.dt
+        k += ref_steps
+    el = time.perf_counter() - t0
+    value = st.n * ref_steps * args.steps / el
+    sample = (f"{st.n} particles (first 512 ids of each lambda ensemble) x {ref_steps} steps per "
+              f"bench step, FP64 oracle, {cores} host threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(wl, sum(e.count for e in wl.ensembles)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    from paper_2403_06706_gb300 import gcpush
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gcpush.build()
+    wl = workload()
+    n_rank = wl.n_particles
+    nodes = synth.wind_grid(wl.wind, dtype=np.float32)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------- device-resident FP32 path ---------------------------------------
+    ctx = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wl.seed,
+                         dt_init=wl.dt, id_base=rank * n_rank)
+    ctx.field_load(nodes, wl.wind.r_min_au, wl.wind.r_max_au)
+    ctx.inject(list(wl.ensembles))
+    ctx.set_launch(**LAUNCH)
+    ctx.tally_arm(**TALLY)
+    for _ in range(args.warmup):
+        ctx.advance(wl.dt, PUSH_STEPS)
+    torch.cuda.synchronize()
+    s0 = ctx.stats()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.advance(wl.dt, PUSH_STEPS)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    el_ms = ev0.elapsed_time(ev1)
+    s1 = ctx.stats()
+    if dist is not None:
+        t = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * n_rank * PUSH_STEPS * args.steps / (el_ms / 1e3)
+    launches = s1["push_launches"] - s0["push_launches"]
+    push_ms = (s1["push_ms"] - s0["push_ms"]) / max(launches, 1)
+    steps_per_launch = PUSH_STEPS * args.steps / max(launches, 1)
+    achieved = FLOP_PER_PSTEP * n_rank * steps_per_launch / (push_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": PUSH_TRAFFIC_BYTES,
+                "kernel": "push_kernel<float>", "launch_ms": push_ms,
+                "flop_per_particle_step": FLOP_PER_PSTEP,
+                "peak_basis": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)",
+                "push_share_of_step": (s1["push_ms"] - s0["push_ms"]) / el_ms}
+    gpu_launches = s1["kernel_launches"] - s0["kernel_launches"]
+    clocks = clk.summary()
+
+    # ---------------- end to end through host buffers ---------------------------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = lambda shape, dt: torch.empty(shape, dtype={np.float64: torch.float64,
+                                                              np.uint32: torch.int32}[dt],
+                                               pin_memory=True).numpy().view(dt)
+        host = gcpush.state_buffers(ctx.n, alloc=pinned)
+        ctx.get_state(out=host)
+        tally_bytes = sum(v.nbytes for v in ctx.tally_read().values())
+        k_e2e = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ctx.set_state(host)
+            ctx.advance(wl.dt, PUSH_STEPS)
+            ctx.get_state(out=host)
+            ctx.tally_read()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nb = gcpush.state_nbytes(host)
+        e2e = {"value": world * n_rank * PUSH_STEPS * k_e2e / el, "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + tally_bytes,
+               "steps": k_e2e,
+               "api": "gc_particles_set (pinned host) + gc_advance + gc_particles_get + gc_tally"}
+    ctx.close()
+
+    # ---------------- plain FP64 path on the same workload ----------------------------
+    fp64 = None
+    if not args.no_fp64:
+        c64 = gcpush.Context(precision=gcpush.PREC_FP64, device=local, stream=stream, seed=wl.seed,
+                             dt_init=wl.dt, id_base=rank * n_rank)
+        c64.field_load(nodes, wl.wind.r_min_au, wl.wind.r_max_au)
+        c64.inject(list(wl.ensembles))
+        c64.set_launch(**LAUNCH)
+        n64 = 40
+        c64.advance(wl.dt, n64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c64.advance(wl.dt, n64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fp64 = {"value": world * n_rank * n64 / (ms / 1e3), "unit": UNIT, "push_steps": n64,
+                "note": "same workload, FP64 grid and arithmetic; timed after the same start-up"}
+        c64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, nodes)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Parker + solenoidal perturbation grid; injected electrons)",
+            "config": config_dict(wl, n_rank),
+            "parallelism": f"particles sharded by id, {world} GPU(s), no data-path collective",
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clocks, "fp64_plain": fp64,
+            "accuracy": "FP32 path within 1e-4 of the FP64 oracle over the first 1e3 steps; "
+                        "FP64 path within 1e-9 (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)",
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

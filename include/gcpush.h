@@ -1,0 +1,212 @@
+/*
+ * gcpush.h -- C ABI of libgcpush, a GB300 (sm_103a) implementation of the
+ * guiding-centre transport of solar energetic electrons of Houeibib,
+ * Pantellini & Griton, "Dynamics of energetic electrons scattered in the solar
+ * wind" (A&A, arXiv:2403.06706).
+ *
+ * Conventions for every entry point
+ *   - All functions return an int status: GC_OK (0) or a negative GC_ERR_*.
+ *     gc_last_error() returns a message for the calling thread's last error.
+ *     Errors never abort the process and never trap the GPU: device-side
+ *     anomalies (non-finite state, positions far outside the grid) set flags
+ *     that gc_advance reports as GC_ERR_DEVICE_ANOMALY after its work is done.
+ *   - Host pointers are caller-owned and are only read or written during the
+ *     call. Device copies of the field and of the particle state are owned by
+ *     the context and freed by gc_destroy.
+ *   - Units at the boundary: descriptors use AU, keV, degrees and seconds;
+ *     particle state and grid values are SI (m, m/s, J/T, T, V/m).
+ *   - Work is issued on the context's CUDA stream (gc_options.stream). Calls
+ *     that return data to the host synchronise that stream before returning.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GCPUSH_H
+#define GCPUSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gc_ctx gc_ctx;
+
+enum {
+    GC_OK = 0,
+    GC_ERR_INVALID = -1,        /* bad argument, size or descriptor */
+    GC_ERR_CUDA = -2,           /* a CUDA runtime call failed (message has the detail) */
+    GC_ERR_NOMEM = -3,          /* device or pinned host allocation failed */
+    GC_ERR_STATE = -4,          /* call out of order (e.g. advance before field_load) */
+    GC_ERR_DEVICE_ANOMALY = -5, /* particles were flagged during the call (see gc_stats) */
+    GC_ERR_UNSUPPORTED = -6     /* feature not available in this build or precision */
+};
+
+/* precision of the push */
+enum {
+    GC_PREC_FP64 = 0,      /* all arithmetic in FP64 */
+    GC_PREC_FP32_MIXED = 1 /* FP32 field and right-hand side; position, gamma v_par and the
+                              free path accumulated in double-float (two FP32 words) */
+};
+
+/* grid node value type */
+enum { GC_DTYPE_F64 = 0, GC_DTYPE_F32 = 1 };
+
+/* per-particle flag bits */
+enum { GC_FLAG_OUT_OF_GRID = 1, GC_FLAG_AXIS = 2, GC_FLAG_NONFINITE = 4 };
+
+typedef struct {
+    int32_t precision;      /* GC_PREC_* */
+    int32_t device;         /* CUDA device ordinal */
+    void *stream;           /* cudaStream_t used for all work; NULL = legacy default stream */
+    uint32_t seed;          /* Philox key word 1 (word 0 is the particle id) */
+    int32_t collision_form; /* 0: exponential free path (default); 1: per-step draw of Eq. 9 */
+    int32_t drift_mask;     /* 0: full Eqs. 1-2; 1: dR/dt = v_par b only */
+    int32_t no_scatter;     /* 1: collisions off */
+    int32_t no_rebirth;     /* 1: rebirth off */
+    uint32_t id_base;       /* id of the first injected particle (shards of one run use
+                               disjoint id ranges, so their Philox streams differ) */
+    double charge;          /* particle charge, C (0 selects the electron, -e) */
+    double mass;            /* rest mass, kg (0 selects the electron mass) */
+    double dt_init;         /* step (s) used to build the start-up history at injection */
+} gc_options;
+
+/* Spherical grid of node values, Sect. 2.2 (trilinear interpolation of the field at the
+ * particle position). Node (i_r, i_theta, i_phi) sits at r = r_min + i_r dr
+ * (dr = (r_max - r_min)/(n_r - 1)), theta = i_theta pi/(n_th - 1) (poles included),
+ * phi = 2 pi i_phi / n_ph (periodic). Layout: [n_ph][n_th][n_r][8] with channels
+ * Bx, By, Bz (T), Ex, Ey, Ez (V/m), |B| (T), Phi (V, unused by ideal fields); vector
+ * components are Cartesian. */
+typedef struct {
+    int32_t n_r, n_th, n_ph;
+    int32_t dtype;          /* GC_DTYPE_*; FP32_MIXED contexts convert F64 data to F32 */
+    double r_min_au, r_max_au;
+    int32_t ideal;          /* 1: E_par := 0 after interpolation (ideal Ohm's law) */
+    int32_t pad0;
+} gc_grid_desc;
+
+/* One ensemble (Sect. 3): count electrons injected at one site, all with one energy or a
+ * power-law spectrum; mu0 and the spectrum draws come from each particle's Philox stream.
+ * Particles are reborn at the site with their initial momentum when they leave
+ * [r_in, r_out]. Ids are assigned contiguously across ensembles in call order. */
+typedef struct {
+    int64_t count;
+    double r0_au, lat_deg, lon_deg; /* injection site */
+    double E0_keV;                  /* mono-energetic kinetic energy */
+    double E_lo_keV, E_hi_keV, E_index; /* spectrum dN/dE ~ E^-index on [E_lo, E_hi] */
+    double lambda_au;               /* field-aligned mean free path (Sect. 2.3) */
+    double r_in_au, r_out_au;       /* shell; r_in <= 0 selects r0 */
+    int32_t energy_law;             /* 0: mono, 1: power law */
+    int32_t mu_law;                 /* 0: mu0 uniform on (0, 1]; 1: mu0 = 1 */
+    int32_t scatter_law;            /* 0: mu = 1 - 2a (Eq. 10); 1: mu = +-sqrt(a) (Eq. 12) */
+    int32_t pad0;
+} gc_ensemble_desc;
+
+/* Snapshot tallies (Sect. 3): every `cadence` steps of the global step counter, each
+ * particle born at t >= t_start adds one sample. */
+typedef struct {
+    int32_t cadence, n_mu, n_E, n_r, n_age, pad0;
+    double t_start_s;
+    double E_lo_keV, E_hi_keV; /* log-spaced energy bins */
+    double r_lo_au, r_hi_au;   /* linear radial bins */
+    double age_max_s;          /* linear age bins on [0, age_max) */
+    double rwin_lo_au, rwin_hi_au; /* window of the age-energy and young-PAD tallies */
+    double age_young_s;        /* young-PAD: age < age_young and >= 1 collision */
+} gc_tally_desc;
+
+/* Host buffers for gc_tally (caller-owned; sizes follow the armed descriptor, n_ens is
+ * the number of ensembles injected so far). */
+typedef struct {
+    uint32_t *h_mer;  /* [n_ens][n_mu][n_E][n_r] counts */
+    uint32_t *h_age;  /* [n_ens][n_age][n_E] counts in the radial window */
+    uint32_t *h_pad;  /* [n_ens][n_mu] young particles with >= 1 collision in the window */
+    uint64_t *m_cnt;  /* [n_ens][n_r] samples per radial bin */
+    uint64_t *m_sin2; /* [n_ens][n_r] sum of sin^2(alpha) in units of 2^-32 */
+    uint64_t *n_seen; /* [2] samples taken, samples outside the mu-E-r ranges */
+} gc_tally_out;
+
+/* Structure-of-arrays particle state (host, caller-owned, n entries each; F0/F1 are
+ * [4][n]: dR/dt (3) and d(gamma v_par)/dt of F^n and F^{n-1}). */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z;  /* guiding-centre position, m */
+    double *u;          /* gamma v_par, m/s */
+    double *mub;        /* magnetic moment, J/T */
+    double *F0, *F1;    /* [4][n] */
+    double *vpar;       /* v_par at the current state, m/s */
+    double *s_rem;      /* remaining free path, m */
+    double *h_prev;     /* step that separates X^{n-1} from X^n, s */
+    double *t_birth;    /* time of (re)birth, s */
+    double *u_inj, *mub_inj; /* injection momentum, restored at rebirth */
+    uint32_t *id, *ens, *event, *ncoll, *flags;
+} gc_particle_soa;
+
+typedef struct {
+    int64_t n_particles;
+    int64_t step;           /* global step counter */
+    double t;               /* simulated time, s */
+    uint64_t particle_steps;
+    uint64_t collisions;
+    uint64_t rebirths;
+    uint32_t flags_or;      /* OR of all particle flags seen */
+    uint32_t pad0;
+    uint64_t kernel_launches; /* kernels this context launched */
+    uint64_t push_launches;   /* launches of the push kernel */
+    double push_ms;           /* summed device time of those launches (CUDA events) */
+    uint64_t sorts;           /* cell sorts performed */
+    double sort_ms;           /* summed device time of the sorts */
+} gc_stats_out;
+
+/* Create a context on opt->device. *out receives the handle. */
+int gc_create(gc_ctx **out, const gc_options *opt);
+void gc_destroy(gc_ctx *ctx);
+/* Message of the calling thread's last error ("" if none). Valid until the next call. */
+const char *gc_last_error(void);
+
+/* Copy the field grid into context-owned device memory. data points to
+ * n_ph*n_th*n_r*8 values of g->dtype, on the host, or on this device if
+ * data_on_device != 0 (then read on the context's stream). */
+int gc_field_load(gc_ctx *ctx, const gc_grid_desc *g, const void *data, int data_on_device);
+
+/* Inject the ensembles (Sect. 3) at the current time; needs a loaded field. Each
+ * particle's mu0 (and energy for a spectrum) comes from Philox events 0 and 1 of its
+ * stream; its free path is drawn, and the start-up history is built with dt_init. */
+int gc_particles_inject(gc_ctx *ctx, const gc_ensemble_desc *e, int n_ens);
+
+/* Advance every particle by n_steps steps of dt seconds (Eqs. 1-6), with scattering
+ * (Eqs. 9-10/12), rebirth and the armed tallies. lambda_au > 0 overrides every
+ * ensemble's mean free path for this call; <= 0 uses the per-ensemble values.
+ * Synchronises the stream; GC_ERR_DEVICE_ANOMALY if any particle was flagged. */
+int gc_advance(gc_ctx *ctx, double dt, int64_t n_steps, double lambda_au);
+
+/* Tallies. If out != NULL the current counts are copied to the host first; then, if
+ * arm != NULL, the tallies are (re)armed with that descriptor and zeroed. */
+int gc_tally(gc_ctx *ctx, const gc_tally_desc *arm, gc_tally_out *out);
+
+/* Copy the particle state to / from host arrays (in id order of the last set/inject;
+ * the library may reorder particles internally, get returns them in that order). */
+int gc_particles_get(gc_ctx *ctx, gc_particle_soa *out_host);
+int gc_particles_set(gc_ctx *ctx, const gc_particle_soa *in_host);
+
+/* Counters and time. */
+int gc_stats(gc_ctx *ctx, gc_stats_out *out);
+
+/* Set the simulated time (s) and the global step counter, e.g. when resuming from a
+ * checkpoint written with gc_particles_get; tally cadence and birth times follow them. */
+int gc_set_clock(gc_ctx *ctx, double t, int64_t step);
+
+/* Launch shape: threads per block (0 = default), steps per kernel launch (0 = default),
+ * and the period of the cell sort in steps (0 = never). */
+int gc_set_launch(gc_ctx *ctx, int block, int steps_per_launch, int sort_every);
+
+/* Sort the particles by grid cell now (results are unchanged: every random draw is keyed
+ * by particle id and every tally is an integer sum). */
+int gc_sort(gc_ctx *ctx);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int gc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCPUSH_H */

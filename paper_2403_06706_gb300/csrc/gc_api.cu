@@ -1,0 +1,866 @@
+// gc_api.cu -- C ABI of libgcpush (see include/gcpush.h).
+//
+// Host side only: context, device memory ownership, argument checks, launch loop.
+// Every computation on particles runs in the kernels of gc_push.cu / gc_sort.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gcpush.h"
+#include "gc_internal.h"
+#include "gc_sort.h"
+
+namespace {
+
+constexpr double kAU = 1.495978707e11;      // m
+constexpr double kKeV = 1.602176634e-16;    // J
+constexpr double kC = 299792458.0;          // m/s
+constexpr double kQe = -1.602176634e-19;    // electron charge, C
+constexpr double kMe = 9.1093837015e-31;    // electron mass, kg
+constexpr double kPi = 3.14159265358979323846;
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? GC_ERR_NOMEM : GC_ERR_CUDA,          \
+                        "%s: %s", #expr, cudaGetErrorString(e_));                              \
+    } while (0)
+
+#define TRY(expr)                                                                              \
+    do {                                                                                       \
+        int r_ = (expr);                                                                       \
+        if (r_ != GC_OK)                                                                       \
+            return r_;                                                                         \
+    } while (0)
+
+// convert node arrays between precisions on the device
+__global__ void convert_nodes(const double *src, float *dst, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+__global__ void convert_nodes(const float *src, double *dst, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+const int kF64Fields = 13; // x y z u mub vpar s_rem h_prev t_birth u_inj mub_inj + F0, F1 rows
+const int kU32Fields = 5;
+
+} // namespace
+
+struct gc_ctx {
+    gc_options opt{};
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+
+    // field
+    void *d_grid = nullptr;
+    gc_grid_desc grid{};
+    gcp::GridHost gh{};
+    bool has_field = false;
+
+    // particles (structure of arrays; F0/F1 are [4][cap])
+    gcp::StateDev st{};
+    int64_t n = 0, cap = 0;
+    std::vector<gcp::EnsDev> ens;
+    gcp::EnsDev *d_ens = nullptr;
+    int64_t ens_cap = 0;
+    uint32_t next_id = 0;
+
+    // time
+    double t = 0.0;
+    int64_t step = 0;
+
+    // tallies
+    bool tally_on = false;
+    gc_tally_desc tdesc{};
+    gcp::TallyDev tdev{};
+    void *d_tally = nullptr;
+    size_t tally_bytes = 0;
+    size_t off_age = 0, off_pad = 0, off_cnt = 0, off_sin2 = 0, off_seen = 0;
+
+    // status
+    uint32_t *d_flags = nullptr;          // [1]
+    unsigned long long *d_counters = nullptr; // [2]
+    uint32_t *h_flags = nullptr;          // pinned mirror
+    unsigned long long *h_counters = nullptr;
+    uint64_t collisions = 0, rebirths = 0, particle_steps = 0;
+    uint32_t flags_or = 0;
+
+    // instrumentation: CUDA events around push launches and sorts
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> push_ev, sort_ev; // pending (start, stop) pool indices
+    size_t ev_next = 0;
+    uint64_t kernel_launches = 0, push_launches = 0, sorts = 0;
+    double push_ms = 0.0, sort_ms = 0.0;
+
+    // order of the particle slots
+    bool in_id_order = true; // slot k holds the k-th smallest id
+    bool ids_dense = true;   // ids are a permutation of [id_lo, id_lo + n)
+    uint32_t id_lo = 0;
+
+    // launch shape
+    int block = 128;
+    int steps_per_launch = 2000;
+    int sort_every = 0;
+    int64_t steps_since_sort = 0;
+    gcp::SortWork sortw{};
+
+    gcp::PhysHost phys() const
+    {
+        gcp::PhysHost p;
+        p.qm = opt.charge / opt.mass;
+        p.inv_m = 1.0 / opt.mass;
+        p.inv_c2 = 1.0 / (kC * kC);
+        p.drift_mask = opt.drift_mask;
+        return p;
+    }
+};
+
+namespace {
+
+int set_device(gc_ctx *c)
+{
+    CUDA_TRY(cudaSetDevice(c->device));
+    return GC_OK;
+}
+
+void free_state(gcp::StateDev &s)
+{
+    double **d[] = {&s.x, &s.y, &s.z, &s.u, &s.mub, &s.vpar, &s.s_rem, &s.h_prev, &s.t_birth,
+                    &s.u_inj, &s.mub_inj, &s.F0, &s.F1};
+    for (double **p : d) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    uint32_t **u[] = {&s.id, &s.ens, &s.event, &s.ncoll, &s.flags};
+    for (uint32_t **p : u) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+}
+
+// Grow the particle arrays to hold `need` particles, keeping the first c->n.
+int reserve(gc_ctx *c, int64_t need)
+{
+    if (need <= c->cap)
+        return GC_OK;
+    int64_t cap = std::max<int64_t>(need, c->cap + c->cap / 2);
+    gcp::StateDev ns{};
+    double **dd[] = {&ns.x, &ns.y, &ns.z, &ns.u, &ns.mub, &ns.vpar, &ns.s_rem, &ns.h_prev,
+                     &ns.t_birth, &ns.u_inj, &ns.mub_inj};
+    double *const od[] = {c->st.x, c->st.y, c->st.z, c->st.u, c->st.mub, c->st.vpar, c->st.s_rem,
+                          c->st.h_prev, c->st.t_birth, c->st.u_inj, c->st.mub_inj};
+    for (int k = 0; k < 11; ++k) {
+        cudaError_t e = cudaMalloc(dd[k], (size_t)cap * sizeof(double));
+        if (e != cudaSuccess) {
+            free_state(ns);
+            return fail(GC_ERR_NOMEM, "cudaMalloc(%lld particles): %s", (long long)cap, cudaGetErrorString(e));
+        }
+        if (c->n)
+            CUDA_TRY(cudaMemcpyAsync(*dd[k], od[k], (size_t)c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    double **ff[] = {&ns.F0, &ns.F1};
+    double *const of[] = {c->st.F0, c->st.F1};
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMalloc(ff[k], (size_t)cap * 4 * sizeof(double));
+        if (e != cudaSuccess) {
+            free_state(ns);
+            return fail(GC_ERR_NOMEM, "cudaMalloc(F rows): %s", cudaGetErrorString(e));
+        }
+        if (c->n)
+            CUDA_TRY(cudaMemcpy2DAsync(*ff[k], (size_t)cap * sizeof(double), of[k], (size_t)c->cap * sizeof(double),
+                                       (size_t)c->n * sizeof(double), 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    uint32_t **uu[] = {&ns.id, &ns.ens, &ns.event, &ns.ncoll, &ns.flags};
+    uint32_t *const ou[] = {c->st.id, c->st.ens, c->st.event, c->st.ncoll, c->st.flags};
+    for (int k = 0; k < kU32Fields; ++k) {
+        cudaError_t e = cudaMalloc(uu[k], (size_t)cap * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            free_state(ns);
+            return fail(GC_ERR_NOMEM, "cudaMalloc(u32 state): %s", cudaGetErrorString(e));
+        }
+        if (c->n)
+            CUDA_TRY(cudaMemcpyAsync(*uu[k], ou[k], (size_t)c->n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    free_state(c->st);
+    ns.n = c->n;
+    ns.cap = cap;
+    c->st = ns;
+    c->cap = cap;
+    (void)kF64Fields;
+    return GC_OK;
+}
+
+int upload_ensembles(gc_ctx *c)
+{
+    if ((int64_t)c->ens.size() > c->ens_cap) {
+        if (c->d_ens) cudaFree(c->d_ens);
+        c->d_ens = nullptr;
+        c->ens_cap = std::max<int64_t>(64, (int64_t)c->ens.size() * 2);
+        CUDA_TRY(cudaMalloc(&c->d_ens, (size_t)c->ens_cap * sizeof(gcp::EnsDev)));
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->d_ens, c->ens.data(), c->ens.size() * sizeof(gcp::EnsDev),
+                             cudaMemcpyHostToDevice, c->stream));
+    return GC_OK;
+}
+
+void harvest_events(gc_ctx *c);
+
+// read back the status words of the last launches (synchronises the stream)
+int collect_status(gc_ctx *c, bool *anomaly)
+{
+    CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->h_counters, c->d_counters, 2 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    harvest_events(c);
+    const uint32_t f = *c->h_flags;
+    c->flags_or |= f;
+    c->collisions += c->h_counters[0];
+    c->rebirths += c->h_counters[1];
+    CUDA_TRY(cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream));
+    if (anomaly)
+        *anomaly = (f != 0);
+    return GC_OK;
+}
+
+int event_pair(gc_ctx *c, std::pair<int, int> *out)
+{
+    while (c->ev_pool.size() < c->ev_next + 2) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        c->ev_pool.push_back(e);
+    }
+    out->first = (int)c->ev_next;
+    out->second = (int)c->ev_next + 1;
+    c->ev_next += 2;
+    return GC_OK;
+}
+
+// sum the device times of the pending event pairs (the stream must be synchronised)
+void harvest_events(gc_ctx *c)
+{
+    for (auto &p : c->push_ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[p.first], c->ev_pool[p.second]) == cudaSuccess)
+            c->push_ms += ms;
+    }
+    for (auto &p : c->sort_ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[p.first], c->ev_pool[p.second]) == cudaSuccess)
+            c->sort_ms += ms;
+    }
+    c->push_ev.clear();
+    c->sort_ev.clear();
+    c->ev_next = 0;
+}
+
+int do_sort(gc_ctx *c)
+{
+    std::pair<int, int> ev;
+    TRY(event_pair(c, &ev));
+    CUDA_TRY(cudaEventRecord(c->ev_pool[ev.first], c->stream));
+    cudaError_t e = gcp::sort_by_cell(c->sortw, c->st, c->gh, (int)c->ens.size(), c->stream);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? GC_ERR_NOMEM : GC_ERR_CUDA, "cell sort: %s",
+                    cudaGetErrorString(e));
+    CUDA_TRY(cudaEventRecord(c->ev_pool[ev.second], c->stream));
+    c->sort_ev.push_back(ev);
+    c->kernel_launches += gcp::kSortKernels;
+    c->sorts += 1;
+    c->steps_since_sort = 0;
+    c->in_id_order = false;
+    return GC_OK;
+}
+
+void free_tally(gc_ctx *c)
+{
+    if (c->d_tally) cudaFree(c->d_tally);
+    c->d_tally = nullptr;
+    c->tally_on = false;
+    c->tally_bytes = 0;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+} // namespace
+
+extern "C" {
+
+int gc_version(void) { return 100; }
+
+const char *gc_last_error(void) { return g_err.c_str(); }
+
+int gc_create(gc_ctx **out, const gc_options *opt)
+{
+    if (!out || !opt)
+        return fail(GC_ERR_INVALID, "gc_create: null argument");
+    *out = nullptr;
+    if (opt->precision != GC_PREC_FP64 && opt->precision != GC_PREC_FP32_MIXED)
+        return fail(GC_ERR_INVALID, "gc_create: unknown precision %d", opt->precision);
+    if (opt->collision_form < 0 || opt->collision_form > 1 || opt->drift_mask < 0 || opt->drift_mask > 1)
+        return fail(GC_ERR_INVALID, "gc_create: bad collision_form/drift_mask");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (opt->device < 0 || opt->device >= ndev)
+        return fail(GC_ERR_INVALID, "gc_create: device %d not present (%d devices)", opt->device, ndev);
+    gc_ctx *c = new gc_ctx();
+    c->opt = *opt;
+    if (c->opt.charge == 0.0) c->opt.charge = kQe;
+    if (c->opt.mass <= 0.0) c->opt.mass = kMe;
+    if (!(c->opt.dt_init > 0.0)) c->opt.dt_init = 0.5;
+    c->device = opt->device;
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+    c->next_id = opt->id_base;
+    c->id_lo = opt->id_base;
+    int rc = set_device(c);
+    if (rc != GC_OK) { delete c; return rc; }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (cudaMalloc(&c->d_flags, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&c->h_flags, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->h_counters, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        gc_destroy(c);
+        return fail(GC_ERR_NOMEM, "gc_create: status allocation failed");
+    }
+    cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t), c->stream);
+    cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        gc_destroy(c);
+        return fail(GC_ERR_CUDA, "gc_create: stream not usable");
+    }
+    *out = c;
+    return GC_OK;
+}
+
+void gc_destroy(gc_ctx *c)
+{
+    if (!c)
+        return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->d_grid) cudaFree(c->d_grid);
+    free_state(c->st);
+    if (c->d_ens) cudaFree(c->d_ens);
+    free_tally(c);
+    if (c->d_flags) cudaFree(c->d_flags);
+    if (c->d_counters) cudaFree(c->d_counters);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    if (c->h_counters) cudaFreeHost(c->h_counters);
+    gcp::sort_free(c->sortw);
+    for (cudaEvent_t e : c->ev_pool)
+        cudaEventDestroy(e);
+    delete c;
+}
+
+int gc_field_load(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_on_device)
+{
+    if (!c || !g || !data)
+        return fail(GC_ERR_INVALID, "gc_field_load: null argument");
+    if (g->n_r < 2 || g->n_th < 2 || g->n_ph < 2)
+        return fail(GC_ERR_INVALID, "gc_field_load: need n_r, n_th, n_ph >= 2");
+    if (g->dtype != GC_DTYPE_F64 && g->dtype != GC_DTYPE_F32)
+        return fail(GC_ERR_INVALID, "gc_field_load: unknown dtype %d", g->dtype);
+    if (!(g->r_min_au > 0.0) || !(g->r_max_au > g->r_min_au))
+        return fail(GC_ERR_INVALID, "gc_field_load: need 0 < r_min < r_max");
+    const size_t nodes = (size_t)g->n_r * g->n_th * g->n_ph;
+    const size_t nval = nodes * 8;
+    if (nval >= (size_t)1 << 32)
+        return fail(GC_ERR_INVALID, "gc_field_load: %zu node values exceed the 2^32 index range", nval);
+    TRY(set_device(c));
+    const bool want64 = (c->opt.precision == GC_PREC_FP64);
+    const size_t esz = want64 ? sizeof(double) : sizeof(float);
+    const size_t in_esz = (g->dtype == GC_DTYPE_F64) ? sizeof(double) : sizeof(float);
+    if (c->d_grid) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_grid);
+        c->d_grid = nullptr;
+        c->has_field = false;
+    }
+    CUDA_TRY(cudaMalloc(&c->d_grid, nval * esz));
+    const bool same = (want64 == (g->dtype == GC_DTYPE_F64));
+    const cudaMemcpyKind kind = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (same) {
+        CUDA_TRY(cudaMemcpyAsync(c->d_grid, data, nval * esz, kind, c->stream));
+    } else {
+        void *tmp = nullptr;
+        CUDA_TRY(cudaMalloc(&tmp, nval * in_esz));
+        cudaError_t e = cudaMemcpyAsync(tmp, data, nval * in_esz, kind, c->stream);
+        if (e == cudaSuccess) {
+            if (want64)
+                convert_nodes<<<1024, 256, 0, c->stream>>>((const float *)tmp, (double *)c->d_grid, nval);
+            else
+                convert_nodes<<<1024, 256, 0, c->stream>>>((const double *)tmp, (float *)c->d_grid, nval);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess)
+            return fail(GC_ERR_CUDA, "gc_field_load: %s", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->grid = *g;
+    c->gh.nodes = c->d_grid;
+    c->gh.n_r = g->n_r;
+    c->gh.n_th = g->n_th;
+    c->gh.n_ph = g->n_ph;
+    c->gh.ideal = g->ideal;
+    c->gh.is_f64 = want64 ? 1 : 0;
+    c->gh.r_min = g->r_min_au * kAU;
+    c->gh.dr = (g->r_max_au * kAU - g->r_min_au * kAU) / (double)(g->n_r - 1);
+    c->gh.dth = kPi / (double)(g->n_th - 1);
+    c->gh.dph = 2.0 * kPi / (double)g->n_ph;
+    c->has_field = true;
+    return GC_OK;
+}
+
+int gc_particles_inject(gc_ctx *c, const gc_ensemble_desc *e, int n_ens)
+{
+    if (!c || (!e && n_ens > 0) || n_ens < 0)
+        return fail(GC_ERR_INVALID, "gc_particles_inject: bad arguments");
+    if (!c->has_field)
+        return fail(GC_ERR_STATE, "gc_particles_inject: no field loaded");
+    if (c->ens.size() + (size_t)n_ens > 65535)
+        return fail(GC_ERR_INVALID, "gc_particles_inject: more than 65535 ensembles");
+    int64_t total = 0;
+    for (int k = 0; k < n_ens; ++k) {
+        const gc_ensemble_desc &d = e[k];
+        if (d.count < 0 || !(d.r0_au > 0.0) || !(d.lambda_au > 0.0) || !(d.r_out_au > 0.0) ||
+            d.energy_law < 0 || d.energy_law > 1 || d.mu_law < 0 || d.mu_law > 1 ||
+            d.scatter_law < 0 || d.scatter_law > 1)
+            return fail(GC_ERR_INVALID, "gc_particles_inject: bad descriptor %d", k);
+        if (d.energy_law == 0 && !(d.E0_keV > 0.0))
+            return fail(GC_ERR_INVALID, "gc_particles_inject: E0 must be > 0 (descriptor %d)", k);
+        if (d.energy_law == 1 && (!(d.E_lo_keV > 0.0) || !(d.E_hi_keV > d.E_lo_keV) || d.E_index == 1.0))
+            return fail(GC_ERR_INVALID, "gc_particles_inject: bad spectrum (descriptor %d)", k);
+        total += d.count;
+    }
+    if ((uint64_t)c->next_id + (uint64_t)total > 0xFFFFFFFFull)
+        return fail(GC_ERR_INVALID, "gc_particles_inject: particle ids exceed 32 bits");
+    TRY(set_device(c));
+    TRY(reserve(c, c->n + total));
+    const int ens_base = (int)c->ens.size();
+    int64_t first = c->n;
+    for (int k = 0; k < n_ens; ++k) {
+        const gc_ensemble_desc &d = e[k];
+        gcp::EnsDev E{};
+        const double r0 = d.r0_au * kAU;
+        const double lat = d.lat_deg * (kPi / 180.0);
+        const double lon = d.lon_deg * (kPi / 180.0);
+        E.R0[0] = r0 * cos(lat) * cos(lon);
+        E.R0[1] = r0 * cos(lat) * sin(lon);
+        E.R0[2] = r0 * sin(lat);
+        E.lambda = d.lambda_au * kAU;
+        E.r_in = (d.r_in_au > 0.0 ? d.r_in_au : d.r0_au) * kAU;
+        E.r_out = d.r_out_au * kAU;
+        E.E0 = d.E0_keV * kKeV;
+        E.E_lo = d.E_lo_keV * kKeV;
+        E.E_hi = d.E_hi_keV * kKeV;
+        E.E_index = d.E_index;
+        E.first = first;
+        E.count = d.count;
+        E.energy_law = d.energy_law;
+        E.mu_law = d.mu_law;
+        E.scatter_law = d.scatter_law;
+        c->ens.push_back(E);
+        first += d.count;
+    }
+    TRY(upload_ensembles(c));
+    if (total > 0) {
+        gcp::InjectParams P{};
+        P.st = c->st;
+        P.ens = c->d_ens + ens_base;
+        P.n_ens = n_ens;
+        P.ens_base = ens_base;
+        P.slot0 = c->n;
+        P.count = total;
+        P.id0 = c->next_id;
+        P.seed = c->opt.seed;
+        P.t = c->t;
+        P.dt_init = c->opt.dt_init;
+        P.m = c->opt.mass;
+        P.c2 = kC * kC;
+        P.gflags = c->d_flags;
+        CUDA_TRY(gcp::launch_inject(c->opt.precision, c->gh, c->phys(), P, c->stream));
+        c->kernel_launches += 1;
+    }
+    if (c->n == 0) {
+        c->id_lo = c->next_id;
+        c->ids_dense = true;
+        c->in_id_order = true;
+    } else if (c->ids_dense && c->next_id != c->id_lo + (uint32_t)c->n) {
+        c->ids_dense = false; // appended ids do not continue the existing range
+    }
+    c->n += total;
+    c->st.n = c->n;
+    c->next_id += (uint32_t)total;
+    bool anomaly = false;
+    TRY(collect_status(c, &anomaly));
+    if (anomaly)
+        return fail(GC_ERR_DEVICE_ANOMALY, "gc_particles_inject: particles flagged (0x%x)", c->flags_or);
+    return GC_OK;
+}
+
+int gc_set_launch(gc_ctx *c, int block, int steps_per_launch, int sort_every)
+{
+    if (!c)
+        return fail(GC_ERR_INVALID, "gc_set_launch: null context");
+    if (block != 0 && (block < 32 || block > 256 || block % 32 != 0))
+        return fail(GC_ERR_INVALID, "gc_set_launch: block must be a multiple of 32 in [32, 256]");
+    if (steps_per_launch < 0 || sort_every < 0)
+        return fail(GC_ERR_INVALID, "gc_set_launch: negative argument");
+    if (block) c->block = block;
+    if (steps_per_launch) c->steps_per_launch = steps_per_launch;
+    c->sort_every = sort_every;
+    return GC_OK;
+}
+
+int gc_sort(gc_ctx *c)
+{
+    if (!c)
+        return fail(GC_ERR_INVALID, "gc_sort: null context");
+    if (!c->has_field)
+        return fail(GC_ERR_STATE, "gc_sort: no field loaded");
+    TRY(set_device(c));
+    if (c->n < 2)
+        return GC_OK;
+    TRY(do_sort(c));
+    bool anomaly = false;
+    return collect_status(c, &anomaly);
+}
+
+int gc_advance(gc_ctx *c, double dt, int64_t n_steps, double lambda_au)
+{
+    if (!c)
+        return fail(GC_ERR_INVALID, "gc_advance: null context");
+    if (!(dt > 0.0) || !std::isfinite(dt) || n_steps < 0)
+        return fail(GC_ERR_INVALID, "gc_advance: need dt > 0 and n_steps >= 0");
+    if (!c->has_field)
+        return fail(GC_ERR_STATE, "gc_advance: no field loaded");
+    TRY(set_device(c));
+    if (c->n == 0 || n_steps == 0) {
+        c->t += (double)n_steps * dt;
+        c->step += n_steps;
+        return GC_OK;
+    }
+    int nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block);
+    if (nb < 1) nb = 1;
+    const int64_t want = (c->n + c->block - 1) / c->block;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)c->sm_count * nb);
+
+    gcp::PushParams P{};
+    P.st = c->st;
+    P.ens = c->d_ens;
+    P.dt = dt;
+    P.t0 = c->t;
+    P.collision_form = c->opt.collision_form;
+    P.no_scatter = c->opt.no_scatter;
+    P.no_rebirth = c->opt.no_rebirth;
+    P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
+    P.seed = c->opt.seed;
+    P.m = c->opt.mass;
+    P.c2 = kC * kC;
+    P.tally_on = c->tally_on ? 1 : 0;
+    P.tally = c->tdev;
+    P.gflags = c->d_flags;
+    P.counters = c->d_counters;
+    const gcp::PhysHost ph = c->phys();
+
+    int64_t done = 0;
+    while (done < n_steps) {
+        if (c->sort_every > 0 && c->steps_since_sort >= c->sort_every) {
+            TRY(do_sort(c));
+            P.st = c->st;
+        }
+        int64_t chunk = std::min<int64_t>(n_steps - done, c->steps_per_launch);
+        if (c->sort_every > 0)
+            chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, c->sort_every - c->steps_since_sort));
+        P.step0 = c->step + done;
+        P.kbase = done;
+        P.n_steps = (int32_t)chunk;
+        std::pair<int, int> ev;
+        TRY(event_pair(c, &ev));
+        CUDA_TRY(cudaEventRecord(c->ev_pool[ev.first], c->stream));
+        CUDA_TRY(gcp::launch_push(c->opt.precision, c->gh, ph, P, c->block, grid, c->stream));
+        CUDA_TRY(cudaEventRecord(c->ev_pool[ev.second], c->stream));
+        c->push_ev.push_back(ev);
+        c->kernel_launches += 1;
+        c->push_launches += 1;
+        done += chunk;
+        c->steps_since_sort += chunk;
+    }
+    c->t += (double)n_steps * dt;
+    c->step += n_steps;
+    c->particle_steps += (uint64_t)c->n * (uint64_t)n_steps;
+    bool anomaly = false;
+    TRY(collect_status(c, &anomaly));
+    if (anomaly)
+        return fail(GC_ERR_DEVICE_ANOMALY, "gc_advance: particles flagged (0x%x)", c->flags_or);
+    return GC_OK;
+}
+
+int gc_tally(gc_ctx *c, const gc_tally_desc *arm, gc_tally_out *out)
+{
+    if (!c)
+        return fail(GC_ERR_INVALID, "gc_tally: null context");
+    TRY(set_device(c));
+    if (out) {
+        if (!c->tally_on)
+            return fail(GC_ERR_STATE, "gc_tally: tallies are not armed");
+        const gc_tally_desc &t = c->tdesc;
+        const size_t ne = (size_t)c->tdev.n_ens;
+        struct Item { void *dst; size_t off, bytes; } items[] = {
+            {out->h_mer, 0, ne * t.n_mu * t.n_E * t.n_r * 4},
+            {out->h_age, c->off_age, ne * t.n_age * t.n_E * 4},
+            {out->h_pad, c->off_pad, ne * t.n_mu * 4},
+            {out->m_cnt, c->off_cnt, ne * t.n_r * 8},
+            {out->m_sin2, c->off_sin2, ne * t.n_r * 8},
+            {out->n_seen, c->off_seen, 2 * 8},
+        };
+        for (const Item &it : items) {
+            if (!it.dst)
+                continue;
+            CUDA_TRY(cudaMemcpyAsync(it.dst, (char *)c->d_tally + it.off, it.bytes, cudaMemcpyDeviceToHost, c->stream));
+        }
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    if (arm) {
+        const gc_tally_desc &t = *arm;
+        if (t.cadence < 1 || t.n_mu < 1 || t.n_E < 1 || t.n_r < 1 || t.n_age < 1 ||
+            !(t.E_lo_keV > 0.0) || !(t.E_hi_keV > t.E_lo_keV) || !(t.r_hi_au > t.r_lo_au) ||
+            !(t.age_max_s > 0.0))
+            return fail(GC_ERR_INVALID, "gc_tally: bad descriptor");
+        const size_t ne = std::max<size_t>(1, c->ens.size());
+        const size_t b_mer = ne * t.n_mu * t.n_E * t.n_r * 4;
+        const size_t b_age = ne * t.n_age * t.n_E * 4;
+        const size_t b_pad = ne * t.n_mu * 4;
+        const size_t b_r = ne * t.n_r * 8;
+        if ((double)ne * t.n_mu * t.n_E * t.n_r >= 2147483647.0 || (double)ne * t.n_age * t.n_E >= 2147483647.0)
+            return fail(GC_ERR_INVALID, "gc_tally: histogram larger than 2^31 bins");
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        free_tally(c);
+        c->off_age = align_up(b_mer, 256);
+        c->off_pad = align_up(c->off_age + b_age, 256);
+        c->off_cnt = align_up(c->off_pad + b_pad, 256);
+        c->off_sin2 = align_up(c->off_cnt + b_r, 256);
+        c->off_seen = align_up(c->off_sin2 + b_r, 256);
+        c->tally_bytes = c->off_seen + 16;
+        CUDA_TRY(cudaMalloc(&c->d_tally, c->tally_bytes));
+        CUDA_TRY(cudaMemsetAsync(c->d_tally, 0, c->tally_bytes, c->stream));
+        char *base = (char *)c->d_tally;
+        gcp::TallyDev &d = c->tdev;
+        d.cadence = t.cadence;
+        d.n_mu = t.n_mu;
+        d.n_E = t.n_E;
+        d.n_r = t.n_r;
+        d.n_age = t.n_age;
+        d.n_ens = (int)ne;
+        d.t_start = t.t_start_s;
+        d.E_lo = t.E_lo_keV * kKeV;
+        d.log_E_ratio = log((t.E_hi_keV * kKeV) / (t.E_lo_keV * kKeV));
+        d.r_lo = t.r_lo_au * kAU;
+        d.r_span = t.r_hi_au * kAU - t.r_lo_au * kAU;
+        d.age_max = t.age_max_s;
+        d.rwin_lo = t.rwin_lo_au * kAU;
+        d.rwin_hi = t.rwin_hi_au * kAU;
+        d.age_young = t.age_young_s;
+        d.h_mer = (uint32_t *)base;
+        d.h_age = (uint32_t *)(base + c->off_age);
+        d.h_pad = (uint32_t *)(base + c->off_pad);
+        d.m_cnt = (unsigned long long *)(base + c->off_cnt);
+        d.m_sin2 = (unsigned long long *)(base + c->off_sin2);
+        d.n_seen = (unsigned long long *)(base + c->off_seen);
+        c->tdesc = t;
+        c->tally_on = true;
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return GC_OK;
+}
+
+int gc_particles_get(gc_ctx *c, gc_particle_soa *o)
+{
+    if (!c || !o)
+        return fail(GC_ERR_INVALID, "gc_particles_get: null argument");
+    if (o->n != c->n)
+        return fail(GC_ERR_INVALID, "gc_particles_get: buffer holds %lld particles, context %lld",
+                    (long long)o->n, (long long)c->n);
+    TRY(set_device(c));
+    const int64_t n = c->n;
+    if (n == 0)
+        return GC_OK;
+    // Source in ascending id order: the state itself, or its un-permuted copy in the
+    // sort's alternate arrays; only an irregular id set falls back to a host reorder.
+    const gcp::StateDev *src = &c->st;
+    std::vector<int64_t> order;
+    if (!c->in_id_order) {
+        if (c->ids_dense) {
+            cudaError_t e = gcp::unpermute_to_alt(c->sortw, c->st, c->id_lo, c->stream);
+            if (e != cudaSuccess)
+                return fail(GC_ERR_CUDA, "gc_particles_get: %s", cudaGetErrorString(e));
+            c->kernel_launches += gcp::kUnpermuteKernels;
+            src = &c->sortw.alt;
+        } else {
+            std::vector<uint32_t> id(n);
+            CUDA_TRY(cudaMemcpyAsync(id.data(), c->st.id, n * 4, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            order.resize(n);
+            std::iota(order.begin(), order.end(), 0);
+            std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return id[a] < id[b]; });
+        }
+    }
+    const int64_t scap = c->cap;
+    std::vector<double> buf(order.empty() ? 0 : n);
+    std::vector<uint32_t> ubuf(order.empty() ? 0 : n);
+    auto getd = [&](const double *from, double *dst) -> int {
+        if (!dst) return GC_OK;
+        if (order.empty()) {
+            CUDA_TRY(cudaMemcpyAsync(dst, from, n * 8, cudaMemcpyDeviceToHost, c->stream));
+            return GC_OK;
+        }
+        CUDA_TRY(cudaMemcpyAsync(buf.data(), from, n * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (int64_t k = 0; k < n; ++k) dst[k] = buf[order[k]];
+        return GC_OK;
+    };
+    auto getu = [&](const uint32_t *from, uint32_t *dst) -> int {
+        if (!dst) return GC_OK;
+        if (order.empty()) {
+            CUDA_TRY(cudaMemcpyAsync(dst, from, n * 4, cudaMemcpyDeviceToHost, c->stream));
+            return GC_OK;
+        }
+        CUDA_TRY(cudaMemcpyAsync(ubuf.data(), from, n * 4, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (int64_t k = 0; k < n; ++k) dst[k] = ubuf[order[k]];
+        return GC_OK;
+    };
+    TRY(getd(src->x, o->x)); TRY(getd(src->y, o->y)); TRY(getd(src->z, o->z));
+    TRY(getd(src->u, o->u)); TRY(getd(src->mub, o->mub)); TRY(getd(src->vpar, o->vpar));
+    TRY(getd(src->s_rem, o->s_rem)); TRY(getd(src->h_prev, o->h_prev));
+    TRY(getd(src->t_birth, o->t_birth)); TRY(getd(src->u_inj, o->u_inj));
+    TRY(getd(src->mub_inj, o->mub_inj));
+    for (int r = 0; r < 4; ++r) {
+        TRY(getd(src->F0 + r * scap, o->F0 ? o->F0 + r * n : nullptr));
+        TRY(getd(src->F1 + r * scap, o->F1 ? o->F1 + r * n : nullptr));
+    }
+    TRY(getu(src->id, o->id)); TRY(getu(src->ens, o->ens)); TRY(getu(src->event, o->event));
+    TRY(getu(src->ncoll, o->ncoll)); TRY(getu(src->flags, o->flags));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GC_OK;
+}
+
+int gc_particles_set(gc_ctx *c, const gc_particle_soa *in)
+{
+    if (!c || !in || in->n < 0)
+        return fail(GC_ERR_INVALID, "gc_particles_set: bad argument");
+    const double *const dsrc[] = {in->x, in->y, in->z, in->u, in->mub, in->vpar, in->s_rem,
+                                  in->h_prev, in->t_birth, in->u_inj, in->mub_inj, in->F0, in->F1};
+    const uint32_t *const usrc[] = {in->id, in->ens, in->event, in->ncoll, in->flags};
+    for (const double *p : dsrc)
+        if (!p && in->n) return fail(GC_ERR_INVALID, "gc_particles_set: every array is required");
+    for (const uint32_t *p : usrc)
+        if (!p && in->n) return fail(GC_ERR_INVALID, "gc_particles_set: every array is required");
+    const int64_t n = in->n;
+    bool ascending = true;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (in->ens[k] >= c->ens.size())
+            return fail(GC_ERR_INVALID, "gc_particles_set: particle %lld has unknown ensemble %u",
+                        (long long)k, in->ens[k]);
+        if (k && in->id[k] <= in->id[k - 1]) ascending = false;
+        lo = std::min(lo, in->id[k]);
+        hi = std::max(hi, in->id[k]);
+    }
+    bool dense = (n == 0) || ((int64_t)hi - (int64_t)lo + 1 == n);
+    if (dense && !ascending) {
+        std::vector<char> seen(n, 0);
+        for (int64_t k = 0; k < n && dense; ++k) {
+            char &f = seen[in->id[k] - lo];
+            if (f) dense = false;
+            f = 1;
+        }
+    }
+    TRY(set_device(c));
+    c->n = 0;
+    c->st.n = 0;
+    TRY(reserve(c, n));
+    double *const ddst[] = {c->st.x, c->st.y, c->st.z, c->st.u, c->st.mub, c->st.vpar, c->st.s_rem,
+                            c->st.h_prev, c->st.t_birth, c->st.u_inj, c->st.mub_inj};
+    if (n) {
+        for (int k = 0; k < 11; ++k)
+            CUDA_TRY(cudaMemcpyAsync(ddst[k], dsrc[k], n * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpy2DAsync(c->st.F0, c->cap * 8, in->F0, n * 8, n * 8, 4, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpy2DAsync(c->st.F1, c->cap * 8, in->F1, n * 8, n * 8, 4, cudaMemcpyHostToDevice, c->stream));
+        uint32_t *const udst[] = {c->st.id, c->st.ens, c->st.event, c->st.ncoll, c->st.flags};
+        for (int k = 0; k < kU32Fields; ++k)
+            CUDA_TRY(cudaMemcpyAsync(udst[k], usrc[k], n * 4, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    c->n = n;
+    c->st.n = n;
+    c->in_id_order = ascending;
+    c->ids_dense = dense;
+    c->id_lo = n ? lo : c->next_id;
+    if (n && hi >= c->next_id)
+        c->next_id = hi + 1;
+    return GC_OK;
+}
+
+int gc_stats(gc_ctx *c, gc_stats_out *o)
+{
+    if (!c || !o)
+        return fail(GC_ERR_INVALID, "gc_stats: null argument");
+    o->n_particles = c->n;
+    o->step = c->step;
+    o->t = c->t;
+    o->particle_steps = c->particle_steps;
+    o->collisions = c->collisions;
+    o->rebirths = c->rebirths;
+    o->flags_or = c->flags_or;
+    o->pad0 = 0;
+    o->kernel_launches = c->kernel_launches;
+    o->push_launches = c->push_launches;
+    o->push_ms = c->push_ms;
+    o->sorts = c->sorts;
+    o->sort_ms = c->sort_ms;
+    return GC_OK;
+}
+
+int gc_set_clock(gc_ctx *c, double t, int64_t step)
+{
+    if (!c || !std::isfinite(t) || step < 0)
+        return fail(GC_ERR_INVALID, "gc_set_clock: bad argument");
+    c->t = t;
+    c->step = step;
+    return GC_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,387 @@
+// gc_device.cuh -- device building blocks of the guiding-centre push (sm_103a).
+//
+// Field gather (trilinear interpolation, Sect. 2.2), the relativistic guiding-centre
+// right-hand side (Eqs. 1-3), the predictor-corrector weights (Eqs. 5-6), Philox-4x32-10
+// (Salmon et al., SC'11) and the double-float accumulators of the FP32 path.
+//
+// Formulation (not a copy of any listing): the gather keeps the interpolant's derivatives
+// in index space (d/di_r, d/di_theta, d/di_phi per channel) and the Cartesian gradients of
+// the three index coordinates; every Jacobian-vector product the right-hand side needs is
+// contracted in that basis, so no 3x3 Jacobian is ever formed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gcp {
+
+enum : uint32_t { FLAG_OUT_OF_GRID = 1u, FLAG_AXIS = 2u, FLAG_NONFINITE = 4u };
+
+// ----------------------------------------------------------------------------------------
+// Philox-4x32-10: ten rounds of two 32x32 -> 64 multiplies; the two key words are bumped
+// by the Weyl constants 0x9E3779B9 / 0xBB67AE85 before every round but the first.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// A particle's event e: key (particle id, seed), counter (e, 0, 0, 0).
+__device__ __forceinline__ uint4 draw(uint32_t id, uint32_t seed, uint32_t event)
+{
+    return philox4x32_10(make_uint4(event, 0u, 0u, 0u), id, seed);
+}
+
+// 53-bit uniform on (0, 1]: 27 high bits of hi, 26 high bits of lo.
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
+{
+    const unsigned long long a = ((unsigned long long)(hi >> 5) << 26) | (lo >> 6);
+    return ((double)a + 1.0) * 0x1.0p-53;
+}
+
+// ----------------------------------------------------------------------------------------
+// Double-float accumulator (hi + lo, |lo| <= ulp(hi)/2): Knuth's TwoSum followed by a
+// fast renormalisation. Used by the FP32 path for R, gamma v_par and the free path.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_add(df a, float b)
+{
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    e = __fadd_rn(e, a.lo);
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// ----------------------------------------------------------------------------------------
+// precision helpers
+__device__ __forceinline__ float m_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double m_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_floor(float a) { return floorf(a); }
+__device__ __forceinline__ double m_floor(double a) { return floor(a); }
+__device__ __forceinline__ float m_rcp(float a) { return 1.0f / a; }
+__device__ __forceinline__ double m_rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ bool m_finite(float a) { return isfinite(a); }
+__device__ __forceinline__ bool m_finite(double a) { return isfinite(a); }
+template <typename T> __device__ __forceinline__ T two_pi();
+template <> __device__ __forceinline__ float two_pi<float>() { return 6.28318530717958647692f; }
+template <> __device__ __forceinline__ double two_pi<double>() { return 6.28318530717958647692; }
+
+// ----------------------------------------------------------------------------------------
+// Grid description in the precision of the push.
+template <typename T>
+struct GridMeta {
+    const T *nodes;   // [n_ph][n_th][n_r][8]
+    int n_r, n_th, n_ph, ideal;
+    T r_min, inv_dr, inv_dth, inv_dph;
+};
+
+// Interpolated field at one point.
+//   B, E: values; dB[d][c], dE[d][c]: derivative of Cartesian component c along index
+//   direction d (0 = i_r, 1 = i_theta, 2 = i_phi); g[d]: Cartesian gradient of index
+//   coordinate d, so dF_c/dx_j = sum_d dF[d][c] g[d][j].
+template <typename T>
+struct Sample {
+    T B[3], E[3];
+    T dB[3][3], dE[3][3];
+    T g[3][3];
+    uint32_t flags;
+};
+
+__device__ __forceinline__ void load_node(const float *__restrict__ p, float v[6])
+{
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float2 b = __ldg(reinterpret_cast<const float2 *>(p + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+
+__device__ __forceinline__ void load_node(const double *__restrict__ p, double v[6])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+    const double2 c = __ldg(reinterpret_cast<const double2 *>(p + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
+// Trilinear interpolation in (r, theta, phi) index space with the index-space gradient of
+// the interpolant (Sect. 2.2). Node-centred grid, poles included in theta, periodic in phi.
+// Positions more than one radial cell outside the grid are flagged; beyond the edge nodes
+// the interpolant is extended as a constant.
+template <typename T>
+__device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sample<T> &s)
+{
+    uint32_t flags = 0;
+    const T rho2 = x * x + y * y;
+    T rho = m_sqrt(rho2);
+    const T r = m_sqrt(rho2 + z * z);
+    if (!(rho > T(1e-30))) {
+        flags |= FLAG_AXIS;
+        rho = T(1e-30);
+    }
+    const T theta = m_atan2(rho, z);
+    T phi = m_atan2(y, x);
+    if (phi < T(0))
+        phi += two_pi<T>();
+    T xr = (r - gm.r_min) * gm.inv_dr;
+    T xt = theta * gm.inv_dth;
+    T xp = phi * gm.inv_dph;
+    if (!(m_finite(xr) && m_finite(xt) && m_finite(xp))) {
+        flags |= FLAG_NONFINITE;
+        xr = T(0); xt = T(0); xp = T(0);
+    }
+    if (xr < T(-1) || xr > T(gm.n_r))
+        flags |= FLAG_OUT_OF_GRID;
+
+    int i = (int)m_floor(xr);
+    T fr = xr - T(i);
+    if (i < 0) { i = 0; fr = T(0); }
+    else if (i > gm.n_r - 2) { i = gm.n_r - 2; fr = T(1); }
+    int j = (int)m_floor(xt);
+    T ft = xt - T(j);
+    if (j < 0) { j = 0; ft = T(0); }
+    else if (j > gm.n_th - 2) { j = gm.n_th - 2; ft = T(1); }
+    int k = (int)m_floor(xp);
+    const T fp = xp - T(k);
+    if (k >= gm.n_ph) k -= gm.n_ph;
+    if (k < 0) k += gm.n_ph;
+    const int k1 = (k + 1 == gm.n_ph) ? 0 : k + 1;
+
+    const uint32_t nr8 = (uint32_t)gm.n_r * 8u;
+    const uint32_t o0 = (((uint32_t)k * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
+    const uint32_t o1 = (((uint32_t)k1 * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
+
+    // c[b][cc][a][ch]: a = r offset, b = theta offset, cc = phi offset
+    T c[2][2][2][6];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const T *p = gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
+            load_node(p, c[b][cc][0]);
+            load_node(p + 8, c[b][cc][1]);
+        }
+    }
+
+#pragma unroll
+    for (int ch = 0; ch < 6; ++ch) {
+        // along r: value and d/di_r on the four (theta, phi) edges
+        T L[2][2], D[2][2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const T d = c[b][cc][1][ch] - c[b][cc][0][ch];
+                D[b][cc] = d;
+                L[b][cc] = c[b][cc][0][ch] + fr * d;
+            }
+        // along theta
+        T V[2], Dr[2], Dt[2];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const T dl = L[1][cc] - L[0][cc];
+            V[cc] = L[0][cc] + ft * dl;
+            Dt[cc] = dl;
+            Dr[cc] = D[0][cc] + ft * (D[1][cc] - D[0][cc]);
+        }
+        // along phi
+        const T dv = V[1] - V[0];
+        const T val = V[0] + fp * dv;
+        const T d_r = Dr[0] + fp * (Dr[1] - Dr[0]);
+        const T d_t = Dt[0] + fp * (Dt[1] - Dt[0]);
+        if (ch < 3) {
+            s.B[ch] = val; s.dB[0][ch] = d_r; s.dB[1][ch] = d_t; s.dB[2][ch] = dv;
+        } else {
+            s.E[ch - 3] = val; s.dE[0][ch - 3] = d_r; s.dE[1][ch - 3] = d_t; s.dE[2][ch - 3] = dv;
+        }
+    }
+
+    // Cartesian gradients of the index coordinates: rhat/dr, thetahat/(r dtheta),
+    // phihat/(r sin(theta) dphi)
+    const T inv_r = m_rcp(r), inv_rho = m_rcp(rho);
+    const T sr = inv_r * gm.inv_dr;
+    s.g[0][0] = x * sr; s.g[0][1] = y * sr; s.g[0][2] = z * sr;
+    const T st = inv_r * inv_r * gm.inv_dth;
+    const T zr = z * inv_rho;
+    s.g[1][0] = zr * x * st; s.g[1][1] = zr * y * st; s.g[1][2] = -rho * st;
+    const T sp = inv_rho * inv_rho * gm.inv_dph;
+    s.g[2][0] = -y * sp; s.g[2][1] = x * sp; s.g[2][2] = T(0);
+    s.flags = flags;
+}
+
+// ----------------------------------------------------------------------------------------
+// Relativistic guiding-centre right-hand side, Eqs. 1-2 (Eq. 3: mu_B constant).
+template <typename T>
+struct Phys {
+    T qm;     // q / m
+    T inv_m;  // 1 / m
+    T inv_c2; // 1 / c^2
+    int drift_mask;
+};
+
+template <typename T>
+struct Aux {
+    T gamma, vpar, Bm;
+};
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename T>
+__device__ __forceinline__ T dot3(const T a[3], const T b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// J w for the channel block dF (J_cj = sum_d dF[d][c] g[d][j]) given p_d = g[d].w
+template <typename T>
+__device__ __forceinline__ void jvec(const T dF[3][3], const T p[3], T out[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        out[c] = dF[0][c] * p[0] + dF[1][c] * p[1] + dF[2][c] * p[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int ideal, T u, T mub,
+                                    T F[4], Aux<T> &aux)
+{
+    const T B2 = dot3(s.B, s.B);
+    const T Bm = m_sqrt(B2);
+    const T inv_B = m_rcp(Bm);
+    const T inv_B2 = inv_B * inv_B;
+    T b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        b[c] = s.B[c] * inv_B;
+
+    // index-space projections of b
+    T pb[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        pb[d] = dot3(s.g[d], b);
+    T JBb[3], JEb[3];
+    jvec(s.dB, pb, JBb);
+    jvec(s.dE, pb, JEb);
+    // grad|B| = J_B^T b
+    T sb[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        sb[d] = s.dB[d][0] * b[0] + s.dB[d][1] * b[1] + s.dB[d][2] * b[2];
+    T gB[3];
+#pragma unroll
+    for (int jx = 0; jx < 3; ++jx)
+        gB[jx] = sb[0] * s.g[0][jx] + sb[1] * s.g[1][jx] + sb[2] * s.g[2][jx];
+    const T b_gB = dot3(b, gB);
+    // curvature (b.grad)b = (J_B b - b (b.grad|B|)) / |B|
+    T kap[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        kap[c] = (JBb[c] - b[c] * b_gB) * inv_B;
+
+    // E x B drift and its directional derivatives
+    T vE[3];
+    cross3(s.E, s.B, vE);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        vE[c] *= inv_B2;
+    T pv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        pv[d] = dot3(s.g[d], vE);
+    T JBv[3], JEv[3];
+    jvec(s.dB, pv, JBv);
+    jvec(s.dE, pv, JEv);
+    const T v_gB = dot3(vE, gB);
+    // (v_E.grad) b
+    T vgb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        vgb[c] = (JBv[c] - b[c] * v_gB) * inv_B;
+    // (w.grad) v_E = ((J_E w) x B + E x (J_B w)) / B^2 - 2 v_E (w.grad|B|) / |B|
+    T t1[3], t2[3], bgv[3], vgv[3];
+    cross3(JEb, s.B, t1);
+    cross3(s.E, JBb, t2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        bgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * b_gB * inv_B;
+    cross3(JEv, s.B, t1);
+    cross3(s.E, JBv, t2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        vgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * v_gB * inv_B;
+
+    const T Epar = ideal ? T(0) : dot3(s.E, b);
+    const T gamma = m_sqrt(T(1) + (u * u + T(2) * mub * Bm * ph.inv_m) * ph.inv_c2);
+    const T inv_g = m_rcp(gamma);
+    const T vpar = u * inv_g;
+
+    if (ph.drift_mask == 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            F[c] = vpar * b[c];
+        F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB;
+    } else {
+        // Eq. 1 bracket
+        const T c_gB = mub * ph.inv_m * inv_g * inv_g;
+        const T c_vE = ph.qm * vpar * Epar * ph.inv_c2 * inv_g;
+        const T v2 = vpar * vpar;
+        T br[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            br[c] = c_gB * gB[c] + c_vE * vE[c] + v2 * kap[c] + vpar * (vgb[c] + bgv[c]) + vgv[c];
+        T bxbr[3];
+        cross3(b, br, bxbr);
+        const T pre = gamma * inv_B / ph.qm;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            F[c] = vpar * b[c] + vE[c] + pre * bxbr[c];
+        // Eq. 2
+        T w[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            w[c] = vpar * kap[c] + vgb[c];
+        F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB + gamma * dot3(vE, w);
+    }
+    aux.gamma = gamma;
+    aux.vpar = vpar;
+    aux.Bm = Bm;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t eval_F(const GridMeta<T> &gm, const Phys<T> &ph, T x, T y, T z,
+                                           T u, T mub, T F[4], Aux<T> &aux)
+{
+    Sample<T> s;
+    gather(gm, x, y, z, s);
+    rhs(s, ph, gm.ideal, u, mub, F, aux);
+    return s.flags;
+}
+
+} // namespace gcp

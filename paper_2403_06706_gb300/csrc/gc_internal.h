@@ -1,0 +1,81 @@
+// gc_internal.h -- structures shared by the host side and the kernels of libgcpush.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gcp {
+
+// One ensemble on the device (SI units). Injection parameters are only read by the
+// injection kernel; the push reads the site, lambda and the shell.
+struct EnsDev {
+    double R0[3];
+    double lambda;       // m
+    double r_in, r_out;  // m
+    double E0, E_lo, E_hi, E_index; // J
+    int64_t first, count; // slot range of the ensemble's particles at injection
+    int32_t energy_law, mu_law, scatter_law, pad;
+};
+
+// Device structure-of-arrays particle state; F0/F1 rows have stride `cap`.
+struct StateDev {
+    double *x, *y, *z, *u, *mub, *F0, *F1, *vpar, *s_rem, *h_prev, *t_birth, *u_inj, *mub_inj;
+    uint32_t *id, *ens, *event, *ncoll, *flags;
+    int64_t n, cap;
+};
+
+struct TallyDev {
+    int32_t cadence, n_mu, n_E, n_r, n_age, n_ens;
+    double t_start, E_lo, log_E_ratio, r_lo, r_span, age_max, rwin_lo, rwin_hi, age_young;
+    uint32_t *h_mer, *h_age, *h_pad;
+    unsigned long long *m_cnt, *m_sin2, *n_seen;
+};
+
+struct PushParams {
+    StateDev st;
+    const EnsDev *ens;
+    double dt, t0;       // t_new = t0 + (kbase + k + 1) dt for local step k
+    int64_t step0;       // global step index of local step 0
+    int64_t kbase;
+    int32_t n_steps;
+    int32_t collision_form, no_scatter, no_rebirth;
+    double lambda_override; // m, > 0 overrides the ensembles
+    uint32_t seed;
+    int32_t tally_on;
+    double m, c2;           // rest mass (kg), c^2
+    TallyDev tally;
+    uint32_t *gflags;              // OR of particle flags raised in this launch
+    unsigned long long *counters;  // [0] collisions, [1] rebirths
+};
+
+struct InjectParams {
+    StateDev st;
+    const EnsDev *ens;
+    int32_t n_ens;        // ensembles of this call (ens points at the first of them)
+    int32_t ens_base;     // global index of ens[0]
+    int64_t slot0, count; // inject slots [slot0, slot0 + count)
+    uint32_t id0;
+    uint32_t seed;
+    double t, dt_init, m, c2;
+    uint32_t *gflags;
+};
+
+} // namespace gcp
+
+// launchers (gc_push.cu)
+namespace gcp {
+struct GridHost {
+    const void *nodes;
+    int n_r, n_th, n_ph, ideal, is_f64;
+    double r_min, dr, dth, dph;
+};
+struct PhysHost {
+    double qm, inv_m, inv_c2;
+    int drift_mask;
+};
+cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, const PushParams &p,
+                        int block, int grid, cudaStream_t s);
+cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
+                          const InjectParams &p, cudaStream_t s);
+int push_max_blocks_per_sm(int precision, int block);
+} // namespace gcp
