@@ -83,8 +83,9 @@ def momentum_scale(st, nodes, wind, ens) -> np.ndarray:
     return np.sqrt(st["u_inj"] ** 2 + 2 * st["mub_inj"] * b / M_E)
 
 
-def compare_states(g, o, tol, pm, skip=None):
-    """Max relative errors of the continuous state; pm: per-particle |p|/m scale."""
+def compare_states(g, o, tol, pm, skip=None, lam=None):
+    """Max relative errors of the continuous state; pm: per-particle |p|/m scale; lam:
+    per-particle mean free path (the scale of the remaining free path; 0.01 AU if None)."""
     keep = np.ones(g["x"].shape[0], dtype=bool) if skip is None else ~skip
     R = np.stack([g["x"], g["y"], g["z"]])[:, keep]
     Ro = np.stack([o["x"], o["y"], o["z"]])[:, keep]
@@ -99,5 +100,6 @@ def compare_states(g, o, tol, pm, skip=None):
         out[F + "_R"] = np.max(np.linalg.norm(g[F][:3, keep] - o[F][:3, keep], axis=0) / v)
         # d(gamma v_par)/dt: the mirror force is ~ v^2 / L ~ (|p|/m) / 1000 s
         out[F + "_u"] = np.max(np.abs(g[F][3, keep] - o[F][3, keep]) / (pm[keep] / 1000.0))
-    out["s_rem"] = np.max(np.abs(g["s_rem"][keep] - o["s_rem"][keep]) / (0.01 * AU))
+    ls = (0.01 * AU) if lam is None else lam[keep]
+    out["s_rem"] = np.max(np.abs(g["s_rem"][keep] - o["s_rem"][keep]) / ls)
     return out

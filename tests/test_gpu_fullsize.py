@@ -46,6 +46,8 @@ def test_full_size_fp32_sampled_parity():
     oracle.advance(f, p, oe, st, 0.0, 0, wl.dt, n_steps)
     div = (gs["ncoll"] != st["ncoll"]) | (gs["event"] != st["event"]) | (gs["t_birth"] != st["t_birth"])
     assert div.mean() <= 0.01, div.sum()
-    err = compare_states(gs, st.arrays, 1e-4, momentum_scale(st, nodes, wl.wind, wl.ensembles), skip=div)
+    lam = np.array([e.lam_au for e in wl.ensembles])[st["ens"].astype(int)] * AU
+    err = compare_states(gs, st.arrays, 1e-4, momentum_scale(st, nodes, wl.wind, wl.ensembles),
+                         skip=div, lam=lam)
     assert max(err.values()) < 1e-4, err
     np.testing.assert_array_equal(gs["flags"], st["flags"])

@@ -27,8 +27,10 @@ R_OUT = synth.r_out_default(WIND)
 ENS = (
     # the paper's site (Sect. 3) with the 4096-electron workload's settings, ragged count
     synth.EnsembleSpec(301, r0_au=0.28, lat_deg=24.0, lam_au=0.5, r_out_au=R_OUT),
-    # short mean free path and a narrow shell: many collisions and rebirths, Eq. 12 law
-    synth.EnsembleSpec(77, r0_au=0.5, lat_deg=-30.0, lon_deg=45.0, E0_keV=40.0, lam_au=0.02,
+    # short mean free path and a narrow shell: many collisions and rebirths, Eq. 12 law.
+    # (Sites are kept off cell faces: the trilinear gradient jumps across a face, and a
+    # point within one ulp of a face is a floating-point tie between two correct values.)
+    synth.EnsembleSpec(77, r0_au=0.5, lat_deg=-30.0, lon_deg=47.0, E0_keV=40.0, lam_au=0.02,
                        r_in_au=0.45, r_out_au=0.6, scatter_law=1),
     # alpha = 0 injection (mu0 = 1) with a power-law spectrum
     synth.EnsembleSpec(19, r0_au=1.0, lat_deg=10.0, lon_deg=200.0, lam_au=0.3, mu_law=1,
@@ -101,7 +103,8 @@ def _fp32_check(g, o, nodes, ens, tol=1e-4, max_diverged=0.01):
     np.testing.assert_array_equal(g["ens"], o["ens"])
     div = (g["ncoll"] != o["ncoll"]) | (g["event"] != o["event"]) | (g["t_birth"] != o["t_birth"])
     assert div.mean() <= max_diverged, div.sum()
-    err = compare_states(g, o.arrays, tol, momentum_scale(o, nodes, WIND, ens), skip=div)
+    err = compare_states(g, o.arrays, tol, momentum_scale(o, nodes, WIND, ens), skip=div,
+                         lam=np.array([e.lam_au for e in ens])[o["ens"].astype(int)] * AU)
     for k, v in err.items():
         assert v < tol, (k, v, err)
     assert np.all(g["flags"] == o["flags"])
