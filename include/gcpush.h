@@ -205,6 +205,44 @@ int gc_sort(gc_ctx *ctx);
 /* Library version (major * 10000 + minor * 100 + patch). */
 int gc_version(void);
 
+/* Device memory gc_advance_noalloc keeps for its own use on every GPU that loads the
+ * library (held until the process exits), and the most ensembles it accepts. */
+#define GC_NOALLOC_SCRATCH_BYTES 32768
+#define GC_NOALLOC_MAX_ENSEMBLES 256
+
+/* gc_advance_noalloc: advance a particle state that lives in the caller's own device
+ * memory, without this library allocating any device memory. The paper has no
+ * counterpart; this is an embedding aid. It is meant for callers that cannot let a
+ * library call cudaMalloc: a simulation code that reserves the GPU's memory for its own
+ * pool and hands out views of its buffers, or a stepping loop that must not pay the
+ * device-wide synchronisation an allocation can cause.
+ *
+ * It runs the push kernel of gc_advance (Eqs. 1-6, scattering, rebirth; no tallies and
+ * no cell sort) on:
+ *   opt       precision, device, stream, seed and the physics switches (dt_init and
+ *             id_base are not used);
+ *   g, grid_dev   the field grid already on the device, in the precision's type (F64 for
+ *             GC_PREC_FP64, F32 for GC_PREC_FP32_MIXED; there is no conversion);
+ *   ens, n_ens    the ensembles the particles were injected with (1..GC_NOALLOC_MAX_
+ *             ENSEMBLES; `count` is ignored); every particle's ens id must be < n_ens;
+ *   state_dev a gc_particle_soa whose pointers are DEVICE addresses (F0/F1 as [4][n]),
+ *             advanced in place, e.g. a copy of what gc_particles_get returned;
+ *   t0, step0 the clock of that state (as gc_stats reports it), then dt, n_steps and
+ *             lambda_au as for gc_advance;
+ *   stats_out optional: collisions, rebirths and flags of this call.
+ * The ensemble table, the anomaly flag and the event counters live in one file-scope
+ * device array of GC_NOALLOC_SCRATCH_BYTES. The first call on a device looks up that
+ * array's device address; make that first call before any stream capture on the device.
+ * Every call overwrites the array (the status words are cleared at the start of each
+ * call), so calls whose work overlaps on the GPU race on it: serialise them. Returns
+ * GC_ERR_INVALID for more ensembles than the maximum, a wrong grid type or an ens id out
+ * of range (checked on the device before the push reads the table), and
+ * GC_ERR_DEVICE_ANOMALY if particles were flagged. It synchronises opt->stream. */
+int gc_advance_noalloc(const gc_options *opt, const gc_grid_desc *g, const void *grid_dev,
+                       const gc_ensemble_desc *ens, int n_ens, const gc_particle_soa *state_dev,
+                       double t0, int64_t step0, double dt, int64_t n_steps, double lambda_au,
+                       gc_stats_out *stats_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,8 @@ const int kU32Fields = 5;
 
 } // namespace
 
+void gcp::set_last_error(const char *msg) { g_err = msg; }
+
 struct gc_ctx {
     gc_options opt{};
     int device = 0;

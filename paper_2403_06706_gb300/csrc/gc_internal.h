@@ -78,4 +78,6 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
 cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
                           const InjectParams &p, cudaStream_t s);
 int push_max_blocks_per_sm(int precision, int block);
+// message returned by gc_last_error() on the calling thread (gc_api.cu)
+void set_last_error(const char *msg);
 } // namespace gcp

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libgcpush.so")
-SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu")
+SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu", "gc_noalloc.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
@@ -129,7 +129,7 @@ class StatsOut(C.Structure):
 
 EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_particles_inject",
            "gc_advance", "gc_tally", "gc_particles_get", "gc_particles_set", "gc_stats",
-           "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock")
+           "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc")
 
 _lib = None
 
@@ -160,6 +160,10 @@ def load(path: str | None = None):
         "gc_sort": (C.c_int, [vp]),
         "gc_version": (C.c_int, []),
         "gc_set_clock": (C.c_int, [vp, C.c_double, C.c_int64]),
+        "gc_advance_noalloc": (C.c_int, [C.POINTER(Options), C.POINTER(GridDesc), vp,
+                                         C.POINTER(EnsembleDesc), C.c_int, C.POINTER(ParticleSoA),
+                                         C.c_double, C.c_int64, C.c_double, C.c_int64, C.c_double,
+                                         C.POINTER(StatsOut)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
