@@ -50,8 +50,8 @@ PUSH_TRAFFIC_BYTES = None
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
 
-def workload():
-    return synth.c2_perturbed()
+def workload(n_per_lambda: int = 1_000_000):
+    return synth.c2_perturbed(n_per_lambda=n_per_lambda)
 
 
 def config_dict(wl, n_per_rank):
@@ -213,6 +213,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--particles", type=int, default=3_000_000,
+                    help="particles per GPU (split over the three lambda ensembles); smaller "
+                         "values are for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -233,7 +236,7 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     gcpush.build()
-    wl = workload()
+    wl = workload(args.particles // 3)
     n_rank = wl.n_particles
     nodes = synth.wind_grid(wl.wind, dtype=np.float32)
     stream = torch.cuda.current_stream()

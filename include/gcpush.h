@@ -207,7 +207,7 @@ int gc_version(void);
 
 /* Device memory gc_advance_noalloc keeps for its own use on every GPU that loads the
  * library (held until the process exits), and the most ensembles it accepts. */
-#define GC_NOALLOC_SCRATCH_BYTES 32768
+#define GC_NOALLOC_SCRATCH_BYTES 40960
 #define GC_NOALLOC_MAX_ENSEMBLES 256
 
 /* gc_advance_noalloc: advance a particle state that lives in the caller's own device

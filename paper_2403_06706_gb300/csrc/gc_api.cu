@@ -493,6 +493,13 @@ int gc_particles_inject(gc_ctx *c, const gc_ensemble_desc *e, int n_ens)
         E.energy_law = d.energy_law;
         E.mu_law = d.mu_law;
         E.scatter_law = d.scatter_law;
+        for (int a = 0; a < 3; ++a) {
+            E.R0_hi[a] = (float)E.R0[a];
+            E.R0_lo[a] = (float)(E.R0[a] - (double)E.R0_hi[a]);
+        }
+        E.r_in2 = (float)(E.r_in * E.r_in);
+        E.r_out2 = (float)(E.r_out * E.r_out);
+        E.lambda_f = (float)E.lambda;
         c->ens.push_back(E);
         first += d.count;
     }
@@ -695,6 +702,14 @@ int gc_tally(gc_ctx *c, const gc_tally_desc *arm, gc_tally_out *out)
         d.rwin_lo = t.rwin_lo_au * kAU;
         d.rwin_hi = t.rwin_hi_au * kAU;
         d.age_young = t.age_young_s;
+        d.inv_E_lo_f = (float)(1.0 / d.E_lo);
+        d.E_scale_f = (float)(t.n_E / d.log_E_ratio);
+        d.r_lo_f = (float)d.r_lo;
+        d.r_scale_f = (float)(t.n_r / d.r_span);
+        d.age_scale_f = (float)(t.n_age / d.age_max);
+        d.rwin_lo_f = (float)d.rwin_lo;
+        d.rwin_hi_f = (float)d.rwin_hi;
+        d.age_young_f = (float)d.age_young;
         d.h_mer = (uint32_t *)base;
         d.h_age = (uint32_t *)(base + c->off_age);
         d.h_pad = (uint32_t *)(base + c->off_pad);

@@ -74,20 +74,48 @@ __device__ __forceinline__ df df_add(df a, float b)
 }
 
 // ----------------------------------------------------------------------------------------
-// precision helpers
+// precision helpers. FP64: correctly rounded library functions (the plain path). FP32:
+// fast forms whose few-ulp errors sit far below the FP32 path's 1e-4 tolerance.
 __device__ __forceinline__ float m_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double m_sqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
-__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_rsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double m_rsqrt(double a) { return 1.0 / sqrt(a); }
 __device__ __forceinline__ float m_floor(float a) { return floorf(a); }
 __device__ __forceinline__ double m_floor(double a) { return floor(a); }
-__device__ __forceinline__ float m_rcp(float a) { return 1.0f / a; }
+__device__ __forceinline__ float m_rcp(float a) { return __fdividef(1.0f, a); }
 __device__ __forceinline__ double m_rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ bool m_finite(float a) { return isfinite(a); }
 __device__ __forceinline__ bool m_finite(double a) { return isfinite(a); }
 template <typename T> __device__ __forceinline__ T two_pi();
 template <> __device__ __forceinline__ float two_pi<float>() { return 6.28318530717958647692f; }
 template <> __device__ __forceinline__ double two_pi<double>() { return 6.28318530717958647692; }
+
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+
+// FP32 atan2: reduce to t = min(|x|,|y|) / max(|x|,|y|) in [0, 1], atan(t) ~ t p(t^2) with
+// p of degree 7 fitted for minimal maximum error on [0, 1] (|error| < 4e-8; the fit is
+// reproduced by csrc/atan_coeffs.py), then unfold the octant.
+__device__ __forceinline__ float m_atan2(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float s = t * t;
+    float p = -4.059181749e-03f;
+    p = fmaf(p, s, 2.188265529e-02f);
+    p = fmaf(p, s, -5.594641340e-02f);
+    p = fmaf(p, s, 9.645255098e-02f);
+    p = fmaf(p, s, -1.391013498e-01f);
+    p = fmaf(p, s, 1.994696012e-01f);
+    p = fmaf(p, s, -3.332990914e-01f);
+    p = fmaf(p, s, 9.999993549e-01f);
+    float r = t * p;
+    if (ay > ax) r = 1.57079632679489662f - r;
+    if (x < 0.0f) r = 3.14159265358979324f - r;
+    return copysignf(r, y);
+}
 
 // ----------------------------------------------------------------------------------------
 // Grid description in the precision of the push.
@@ -133,13 +161,14 @@ template <typename T>
 __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sample<T> &s)
 {
     uint32_t flags = 0;
-    const T rho2 = x * x + y * y;
-    T rho = m_sqrt(rho2);
-    const T r = m_sqrt(rho2 + z * z);
-    if (!(rho > T(1e-30))) {
+    T rho2 = x * x + y * y;
+    if (!(rho2 > T(1e-30))) {
         flags |= FLAG_AXIS;
-        rho = T(1e-30);
+        rho2 = T(1e-30);
     }
+    const T r2 = rho2 + z * z;
+    const T inv_rho = m_rsqrt(rho2), inv_r = m_rsqrt(r2);
+    const T rho = rho2 * inv_rho, r = r2 * inv_r;
     const T theta = m_atan2(rho, z);
     T phi = m_atan2(y, x);
     if (phi < T(0))
@@ -219,7 +248,6 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
 
     // Cartesian gradients of the index coordinates: rhat/dr, thetahat/(r dtheta),
     // phihat/(r sin(theta) dphi)
-    const T inv_r = m_rcp(r), inv_rho = m_rcp(rho);
     const T sr = inv_r * gm.inv_dr;
     s.g[0][0] = x * sr; s.g[0][1] = y * sr; s.g[0][2] = z * sr;
     const T st = inv_r * inv_r * gm.inv_dth;
@@ -235,8 +263,10 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
 template <typename T>
 struct Phys {
     T qm;     // q / m
+    T inv_qm; // m / q
     T inv_m;  // 1 / m
     T inv_c2; // 1 / c^2
+    T mc2;    // m c^2
     int drift_mask;
 };
 
@@ -273,8 +303,8 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
                                     T F[4], Aux<T> &aux)
 {
     const T B2 = dot3(s.B, s.B);
-    const T Bm = m_sqrt(B2);
-    const T inv_B = m_rcp(Bm);
+    const T inv_B = m_rsqrt(B2);
+    const T Bm = B2 * inv_B;
     const T inv_B2 = inv_B * inv_B;
     T b[3];
 #pragma unroll
@@ -338,8 +368,10 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         vgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * v_gB * inv_B;
 
     const T Epar = ideal ? T(0) : dot3(s.E, b);
-    const T gamma = m_sqrt(T(1) + (u * u + T(2) * mub * Bm * ph.inv_m) * ph.inv_c2);
-    const T inv_g = m_rcp(gamma);
+    // gamma^2 = 1 + (gamma v)^2 / c^2 with (gamma v)^2 = u^2 + 2 mu_B B / m
+    const T g2 = T(1) + (u * u + T(2) * mub * Bm * ph.inv_m) * ph.inv_c2;
+    const T inv_g = m_rsqrt(g2);
+    const T gamma = g2 * inv_g;
     const T vpar = u * inv_g;
 
     if (ph.drift_mask == 1) {
@@ -358,7 +390,7 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
             br[c] = c_gB * gB[c] + c_vE * vE[c] + v2 * kap[c] + vpar * (vgb[c] + bgv[c]) + vgv[c];
         T bxbr[3];
         cross3(b, br, bxbr);
-        const T pre = gamma * inv_B / ph.qm;
+        const T pre = gamma * inv_B * ph.inv_qm;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             F[c] = vpar * b[c] + vE[c] + pre * bxbr[c];

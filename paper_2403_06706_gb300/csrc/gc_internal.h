@@ -15,6 +15,9 @@ struct EnsDev {
     double E0, E_lo, E_hi, E_index; // J
     int64_t first, count; // slot range of the ensemble's particles at injection
     int32_t energy_law, mu_law, scatter_law, pad;
+    // FP32-path copies, precomputed on the host: R0 as double-float pairs, r_in^2, r_out^2
+    float R0_hi[3], R0_lo[3];
+    float r_in2, r_out2, lambda_f, pad_f;
 };
 
 // Device structure-of-arrays particle state; F0/F1 rows have stride `cap`.
@@ -27,6 +30,8 @@ struct StateDev {
 struct TallyDev {
     int32_t cadence, n_mu, n_E, n_r, n_age, n_ens;
     double t_start, E_lo, log_E_ratio, r_lo, r_span, age_max, rwin_lo, rwin_hi, age_young;
+    // FP32-path forms: 1/E_lo, n_E/ln(E_hi/E_lo), r_lo, n_r/span, n_age/age_max, window, age
+    float inv_E_lo_f, E_scale_f, r_lo_f, r_scale_f, age_scale_f, rwin_lo_f, rwin_hi_f, age_young_f;
     uint32_t *h_mer, *h_age, *h_pad;
     unsigned long long *m_cnt, *m_sin2, *n_seen;
 };

@@ -144,6 +144,13 @@ extern "C" int gc_advance_noalloc(const gc_options *opt, const gc_grid_desc *g, 
         E.energy_law = d.energy_law;
         E.mu_law = d.mu_law;
         E.scatter_law = d.scatter_law;
+        for (int a = 0; a < 3; ++a) {
+            E.R0_hi[a] = (float)E.R0[a];
+            E.R0_lo[a] = (float)(E.R0[a] - (double)E.R0_hi[a]);
+        }
+        E.r_in2 = (float)(E.r_in * E.r_in);
+        E.r_out2 = (float)(E.r_out * E.r_out);
+        E.lambda_f = (float)E.lambda;
         table[k] = E;
     }
     gcp::EnsDev *d_table = reinterpret_cast<gcp::EnsDev *>(scr);

@@ -37,6 +37,30 @@ template <> struct AccOf<float> {
     static __device__ __forceinline__ bool nonpos(A a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo <= 0.0f); }
 };
 
+// FP32-path uniform from one Philox word: u = (k + 1/2) 2^-31 with k the word's top 31
+// bits (the FP64 path's 53-bit draw starts with the same bits, so the two agree to 2^-32),
+// together with its complement 1 - u, each with full float relative precision.
+struct UPair {
+    float u, ub;
+};
+
+__device__ __forceinline__ UPair u31(uint32_t w)
+{
+    const uint32_t k = w >> 1;
+    return {fmaf(__uint2float_rn(k), 0x1p-31f, 0x1p-32f),
+            fmaf(__uint2float_rn(0x7FFFFFFFu - k), 0x1p-31f, 0x1p-32f)};
+}
+
+// -ln(u) without cancellation at either end of (0, 1)
+__device__ __forceinline__ float neg_log_u(UPair p) { return p.u < 0.5f ? -logf(p.u) : -log1pf(-p.ub); }
+
+// Time of the end of local step k. Out of line so that the FP64 arithmetic stays in the
+// rare branches that need it (rebirth, tally) instead of being hoisted into every step.
+__device__ __noinline__ double step_time(double t0, long long kk, double dt)
+{
+    return __dadd_rn(t0, __dmul_rn((double)kk, dt));
+}
+
 // warp-aggregated increment of base[idx] (idx < 0: no increment for this lane)
 __device__ __forceinline__ void agg_inc(uint32_t *base, int idx)
 {
@@ -60,48 +84,61 @@ __device__ __forceinline__ void agg_inc64(unsigned long long *base, int idx)
 // operations as the definition (double); FP32: the same formulas in float, with
 // gamma - 1 formed without cancellation.
 template <typename T>
-__device__ __forceinline__ void tally_sample(const TallyDev &T_, const PushParams &P, uint32_t e, T x,
-                                             T y, T z, T u, T mub, T Bm, double age, uint32_t ncoll,
-                                             bool take)
+__device__ __forceinline__ void tally_sample(const TallyDev &T_, const PushParams &P, const Phys<T> &ph,
+                                             uint32_t e, T x, T y, T z, T u, T mub, T Bm, double age,
+                                             uint32_t ncoll, bool take)
 {
     int im = -1, iE = -1, ir = -1, ia = -1, ipad = -1;
     unsigned long long s2 = 0;
-    bool win = false;
     if (take) {
-        double mu, Ek, r, sin2;
-        if (sizeof(T) == 8) {
-            r = sqrt((double)x * x + (double)y * y + (double)z * z);
+        if constexpr (sizeof(T) == 8) {
+            const double r = sqrt((double)x * x + (double)y * y + (double)z * z);
             const double gv2 = (double)u * u + 2.0 * (double)mub * (double)Bm / P.m;
             const double gamma = sqrt(1.0 + gv2 / P.c2);
-            mu = (double)u / sqrt(gv2);
-            Ek = (gamma - 1.0) * P.m * P.c2;
-            sin2 = 1.0 - mu * mu;
+            const double mu = (double)u / sqrt(gv2);
+            const double Ek = (gamma - 1.0) * P.m * P.c2;
+            const double sin2 = 1.0 - mu * mu;
+            im = (int)floor((mu + 1.0) / 2.0 * T_.n_mu);
+            if (im >= T_.n_mu) im = T_.n_mu - 1;
+            if (im < 0) im = 0;
+            const double xe = log(Ek / T_.E_lo) / T_.log_E_ratio * T_.n_E;
+            iE = (xe >= 0.0 && xe < T_.n_E) ? (int)floor(xe) : -1;
+            const double xr = (r - T_.r_lo) / T_.r_span * T_.n_r;
+            ir = (xr >= 0.0 && xr < T_.n_r) ? (int)floor(xr) : -1;
+            s2 = (unsigned long long)floor(sin2 * 4294967296.0 + 0.5);
+            if (r >= T_.rwin_lo && r < T_.rwin_hi) {
+                const double xa = age / T_.age_max * T_.n_age;
+                if (xa >= 0.0 && xa < T_.n_age && iE >= 0)
+                    ia = (int)(((int64_t)e * T_.n_age + (int)floor(xa)) * T_.n_E + iE);
+                if (age < T_.age_young && ncoll >= 1)
+                    ipad = (int)e * T_.n_mu + im;
+            }
         } else {
+            // FP32 path: the same bins from float arithmetic (gamma - 1 without cancellation)
             const float xf = (float)x, yf = (float)y, zf = (float)z, uf = (float)u;
-            r = (double)sqrtf(xf * xf + yf * yf + zf * zf);
-            const float gv2 = uf * uf + 2.0f * (float)mub * (float)Bm * (float)(1.0 / P.m);
-            const float q = gv2 * (float)(1.0 / P.c2);
+            const float rf = sqrtf(xf * xf + yf * yf + zf * zf);
+            const float gv2 = uf * uf + 2.0f * (float)mub * (float)Bm * (float)ph.inv_m;
+            const float q = gv2 * (float)ph.inv_c2;
             const float gm1 = q / (sqrtf(1.0f + q) + 1.0f);
             const float muf = uf * rsqrtf(gv2);
-            mu = (double)muf;
-            Ek = (double)gm1 * P.m * P.c2;
-            sin2 = (double)(1.0f - muf * muf);
-        }
-        im = (int)floor((mu + 1.0) / 2.0 * T_.n_mu);
-        if (im >= T_.n_mu) im = T_.n_mu - 1;
-        if (im < 0) im = 0;
-        const double xe = log(Ek / T_.E_lo) / T_.log_E_ratio * T_.n_E;
-        iE = (xe >= 0.0 && xe < T_.n_E) ? (int)floor(xe) : -1;
-        const double xr = (r - T_.r_lo) / T_.r_span * T_.n_r;
-        ir = (xr >= 0.0 && xr < T_.n_r) ? (int)floor(xr) : -1;
-        s2 = (unsigned long long)floor(sin2 * 4294967296.0 + 0.5);
-        win = (r >= T_.rwin_lo && r < T_.rwin_hi);
-        if (win) {
-            const double xa = age / T_.age_max * T_.n_age;
-            if (xa >= 0.0 && xa < T_.n_age && iE >= 0)
-                ia = (int)(((int64_t)e * T_.n_age + (int)floor(xa)) * T_.n_E + iE);
-            if (age < T_.age_young && ncoll >= 1)
-                ipad = (int)e * T_.n_mu + im;
+            const float Ekf = gm1 * (float)ph.mc2;
+            const float s2f = 1.0f - muf * muf;
+            im = (int)floorf((muf + 1.0f) * 0.5f * (float)T_.n_mu);
+            if (im >= T_.n_mu) im = T_.n_mu - 1;
+            if (im < 0) im = 0;
+            const float xe = logf(Ekf * T_.inv_E_lo_f) * T_.E_scale_f;
+            iE = (xe >= 0.0f && xe < (float)T_.n_E) ? (int)floorf(xe) : -1;
+            const float xr = (rf - T_.r_lo_f) * T_.r_scale_f;
+            ir = (xr >= 0.0f && xr < (float)T_.n_r) ? (int)floorf(xr) : -1;
+            s2 = (unsigned long long)__float2ull_rn(s2f * 4294967296.0f);
+            if (rf >= T_.rwin_lo_f && rf < T_.rwin_hi_f) {
+                const float agef = (float)age;
+                const float xa = agef * T_.age_scale_f;
+                if (xa >= 0.0f && xa < (float)T_.n_age && iE >= 0)
+                    ia = (int)(((int64_t)e * T_.n_age + (int)floorf(xa)) * T_.n_E + iE);
+                if (agef < T_.age_young_f && ncoll >= 1)
+                    ipad = (int)e * T_.n_mu + im;
+            }
         }
     }
     agg_inc64(T_.n_seen, take ? 0 : -1);
@@ -119,8 +156,15 @@ __device__ __forceinline__ void tally_sample(const TallyDev &T_, const PushParam
 }
 
 // ----------------------------------------------------------------------------------------
+// The per-step work is a loop over evaluation phases so that one copy of the field
+// evaluation serves all of them (instruction-cache footprint):
+//   phase 0  F* at the predictor point (Eq. 5), then the corrector (Eq. 6)
+//   phase 1  F^{n+1} at the corrector point, then free path, rebirth and collision tests
+//   phase 2  F^n of the new state after a rebirth or collision (start-up, Sect. 2.2)
+//   phase 3  F^{n-1} at X^n - dt F^n
+// Phases 2-3 run only for the lanes that restart.
 template <typename T>
-__global__ void __launch_bounds__(256) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                    const PushParams P)
 {
     using Acc = AccOf<T>;
@@ -128,6 +172,9 @@ __global__ void __launch_bounds__(256) push_kernel(const GridMeta<T> gm, const P
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned n_coll = 0, n_reb = 0;
     const T dtT = (T)P.dt;
+    // Eq. 5-6 weights at tau = 1: 3/2, -1/2 (AB2) and 2/3, 5/12, -1/12 (AM3)
+    const T a0_1 = dtT * T(1.5), a1_1 = dtT * T(-0.5);
+    const T c0_1 = dtT * T(2.0 / 3.0), cs_1 = dtT * T(5.0 / 12.0), c1_1 = dtT * T(-1.0 / 12.0);
 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.st.n; i += stride) {
         const int64_t cap = P.st.cap;
@@ -135,6 +182,8 @@ __global__ void __launch_bounds__(256) push_kernel(const GridMeta<T> gm, const P
         const EnsDev &E = P.ens[e];
         const double lambda = P.lambda_override > 0.0 ? P.lambda_override : E.lambda;
         const double r_in = E.r_in, r_out = E.r_out;
+        const float ri2 = E.r_in2, ro2 = E.r_out2;
+        const float lambda_f = P.lambda_override > 0.0 ? (float)P.lambda_override : E.lambda_f;
         const int scatter_law = E.scatter_law;
         const uint32_t id = P.st.id[i];
 
@@ -160,110 +209,157 @@ __global__ void __launch_bounds__(256) push_kernel(const GridMeta<T> gm, const P
         }
 
         for (int k = 0; k < P.n_steps; ++k) {
-            const T tau = dtT / hprev;
-            // Eq. 5
-            const T a0 = dtT * (T(1) + T(0.5) * tau);
-            const T a1 = -dtT * T(0.5) * tau;
-            T Fs[4];
-            Aux<T> axs;
-            flags |= eval_F(gm, ph, Acc::val(Rx) + (a0 * F0[0] + a1 * F1[0]),
-                            Acc::val(Ry) + (a0 * F0[1] + a1 * F1[1]),
-                            Acc::val(Rz) + (a0 * F0[2] + a1 * F1[2]),
-                            Acc::val(U) + (a0 * F0[3] + a1 * F1[3]), mub, Fs, axs);
-            // Eq. 6: weights (3 + tau)/6, (3 + 2 tau)/(6 (1 + tau)), -tau^2/(6 (1 + tau))
-            const T w = dtT / (T(6) * (T(1) + tau));
-            const T c0 = dtT * (T(3) + tau) / T(6);
-            const T cs = w * (T(3) + T(2) * tau);
-            const T c1 = -w * tau * tau;
-            Rx = Acc::add(Rx, c0 * F0[0] + cs * Fs[0] + c1 * F1[0]);
-            Ry = Acc::add(Ry, c0 * F0[1] + cs * Fs[1] + c1 * F1[1]);
-            Rz = Acc::add(Rz, c0 * F0[2] + cs * Fs[2] + c1 * F1[2]);
-            U = Acc::add(U, c0 * F0[3] + cs * Fs[3] + c1 * F1[3]);
-            T F2[4];
-            Aux<T> ax2;
-            flags |= eval_F(gm, ph, Acc::val(Rx), Acc::val(Ry), Acc::val(Rz), Acc::val(U), mub, F2, ax2);
-
-            // Sect. 2.3: path length along B in this step
-            const T ds = dtT * (fabs(vpar0) + fabs(ax2.vpar)) * T(0.5);
-            bool collide = false;
-            if (!P.no_scatter) {
-                if (P.collision_form == 0) {
-                    S = Acc::add(S, -ds);
-                    collide = Acc::nonpos(S);
-                } else {
-                    const uint4 wd = draw(id, P.seed, event++);
-                    collide = u53(wd.x, wd.y) < 1.0 - exp(-(double)ds / lambda);
-                }
+            T a0 = a0_1, a1 = a1_1, c0 = c0_1, cs = cs_1, c1 = c1_1;
+            if (hprev != dtT) {
+                // variable step: tau = dt^n / dt^{n-1}; weights (3+tau)/6,
+                // (3+2 tau)/(6(1+tau)), -tau^2/(6(1+tau)) of Eq. 6
+                const T tau = dtT / hprev;
+                a0 = dtT * (T(1) + T(0.5) * tau);
+                a1 = -dtT * T(0.5) * tau;
+                const T w = dtT / (T(6) * (T(1) + tau));
+                c0 = dtT * (T(3) + tau) / T(6);
+                cs = w * (T(3) + T(2) * tau);
+                c1 = -w * tau * tau;
             }
-            bool reborn = false;
-            if (!P.no_rebirth) {
-                if (sizeof(T) == 8) {
-                    const double xx = Acc::to(Rx), yy = Acc::to(Ry), zz = Acc::to(Rz);
-                    const double r1 = sqrt(xx * xx + yy * yy + zz * zz);
-                    reborn = (r1 < r_in || r1 > r_out);
-                } else {
-                    const float xx = (float)Acc::val(Rx), yy = (float)Acc::val(Ry), zz = (float)Acc::val(Rz);
-                    const float r2 = xx * xx + yy * yy + zz * zz;
-                    const float ri2 = (float)(r_in * r_in), ro2 = (float)(r_out * r_out);
-                    if (fabsf(r2 - ri2) < 1e-5f * ri2 || fabsf(r2 - ro2) < 1e-5f * ro2) {
-                        // near the shell: decide in double from the accumulated position
-                        const double X = Acc::to(Rx), Y = Acc::to(Ry), Z = Acc::to(Rz);
-                        const double r1 = sqrt(X * X + Y * Y + Z * Z);
-                        reborn = (r1 < r_in || r1 > r_out);
-                    } else {
-                        reborn = (r2 < ri2 || r2 > ro2);
+            int n_phase = 2;
+#pragma unroll 1
+            for (int phase = 0; phase < n_phase; ++phase) {
+                T px = Acc::val(Rx), py = Acc::val(Ry), pz = Acc::val(Rz), pu = Acc::val(U);
+                if (phase == 0) {
+                    px += a0 * F0[0] + a1 * F1[0];
+                    py += a0 * F0[1] + a1 * F1[1];
+                    pz += a0 * F0[2] + a1 * F1[2];
+                    pu += a0 * F0[3] + a1 * F1[3];
+                } else if (phase == 3) {
+                    px -= dtT * F0[0];
+                    py -= dtT * F0[1];
+                    pz -= dtT * F0[2];
+                    pu -= dtT * F0[3];
+                }
+                T Fo[4];
+                Aux<T> ax;
+                flags |= eval_F(gm, ph, px, py, pz, pu, mub, Fo, ax);
+
+                if (phase == 0) {
+                    Rx = Acc::add(Rx, c0 * F0[0] + cs * Fo[0] + c1 * F1[0]);
+                    Ry = Acc::add(Ry, c0 * F0[1] + cs * Fo[1] + c1 * F1[1]);
+                    Rz = Acc::add(Rz, c0 * F0[2] + cs * Fo[2] + c1 * F1[2]);
+                    U = Acc::add(U, c0 * F0[3] + cs * Fo[3] + c1 * F1[3]);
+                } else if (phase == 1) {
+                    // Sect. 2.3: path length along B in this step
+                    const T ds = dtT * (fabs(vpar0) + fabs(ax.vpar)) * T(0.5);
+                    bool collide = false;
+                    if (!P.no_scatter) {
+                        if (P.collision_form == 0) {
+                            S = Acc::add(S, -ds);
+                            collide = Acc::nonpos(S);
+                        } else {
+                            // the per-step draw of Eq. 9: collide if a < 1 - exp(-ds / lambda)
+                            const uint4 wd = draw(id, P.seed, event++);
+                            if constexpr (sizeof(T) == 8)
+                                collide = u53(wd.x, wd.y) < 1.0 - exp(-(double)ds / lambda);
+                            else
+                                collide = u31(wd.x).u < -expm1f(-(float)ds / lambda_f);
+                        }
                     }
-                }
-            }
-
-            bool restart = false;
-            if (reborn) {
-                // Sect. 3: reborn at the injection site with the initial velocity
-                Rx = Acc::from(E.R0[0]);
-                Ry = Acc::from(E.R0[1]);
-                Rz = Acc::from(E.R0[2]);
-                U = Acc::from(P.st.u_inj[i]);
-                mub = (T)P.st.mub_inj[i];
-                const uint4 wd = draw(id, P.seed, event++);
-                S = Acc::from(-lambda * log(u53(wd.z, wd.w)));
-                ncoll = 0;
-                t_birth = P.t0 + (double)(P.kbase + k + 1) * P.dt;
-                ++n_reb;
-                restart = true;
-            } else if (collide) {
-                const uint4 wd = draw(id, P.seed, event++);
-                const double a = u53(wd.x, wd.y);
-                const double mu_new = (scatter_law == 0) ? 1.0 - 2.0 * a                   // Eq. 10
-                                                         : ((wd.x & 1u) ? -sqrt(a) : sqrt(a)); // Eq. 12
-                const double Bm = (double)ax2.Bm;
-                const double uu = Acc::to(U);
-                const double pm2 = uu * uu + 2.0 * (double)mub * Bm / P.m;
-                const double pm = sqrt(pm2);
-                U = Acc::from(mu_new * pm);
-                mub = (T)((1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm));
-                if (P.collision_form == 0)
-                    S = Acc::from(-lambda * log(u53(wd.z, wd.w)));
-                ++ncoll;
-                ++n_coll;
-                restart = true;
-            }
-            if (restart) {
-                // Sect. 2.2 start-up: F^n = F(X^n), X^{n-1} = X^n - dt F^n, F^{n-1} = F(X^{n-1})
-                const T x = Acc::val(Rx), y = Acc::val(Ry), z = Acc::val(Rz), uu = Acc::val(U);
-                Aux<T> a0x, a1x;
-                flags |= eval_F(gm, ph, x, y, z, uu, mub, F0, a0x);
-                flags |= eval_F(gm, ph, x - dtT * F0[0], y - dtT * F0[1], z - dtT * F0[2],
-                                uu - dtT * F0[3], mub, F1, a1x);
-                vpar0 = a0x.vpar;
-                Bm0 = a0x.Bm;
-            } else {
+                    bool reborn = false;
+                    if (!P.no_rebirth) {
+                        if (sizeof(T) == 8) {
+                            const double xx = Acc::to(Rx), yy = Acc::to(Ry), zz = Acc::to(Rz);
+                            const double r1 = sqrt(xx * xx + yy * yy + zz * zz);
+                            reborn = (r1 < r_in || r1 > r_out);
+                        } else {
+                            const float xx = (float)px, yy = (float)py, zz = (float)pz;
+                            const float r2 = xx * xx + yy * yy + zz * zz;
+                            if (fabsf(r2 - ri2) < 1e-5f * ri2 || fabsf(r2 - ro2) < 1e-5f * ro2) {
+                                // near the shell: decide in double from the accumulated position
+                                const double X = Acc::to(Rx), Y = Acc::to(Ry), Z = Acc::to(Rz);
+                                const double r1 = sqrt(X * X + Y * Y + Z * Z);
+                                reborn = (r1 < r_in || r1 > r_out);
+                            } else {
+                                reborn = (r2 < ri2 || r2 > ro2);
+                            }
+                        }
+                    }
+                    if (reborn) {
+                        // Sect. 3: reborn at the injection site with the initial velocity
+                        const uint4 wd = draw(id, P.seed, event++);
+                        if constexpr (sizeof(T) == 8) {
+                            Rx = E.R0[0];
+                            Ry = E.R0[1];
+                            Rz = E.R0[2];
+                            S = -lambda * log(u53(wd.z, wd.w));
+                        } else {
+                            Rx = df{E.R0_hi[0], E.R0_lo[0]};
+                            Ry = df{E.R0_hi[1], E.R0_lo[1]};
+                            Rz = df{E.R0_hi[2], E.R0_lo[2]};
+                            S = df{lambda_f * neg_log_u(u31(wd.z)), 0.0f};
+                        }
+                        U = Acc::from(P.st.u_inj[i]);
+                        mub = (T)P.st.mub_inj[i];
+                        ncoll = 0;
+                        t_birth = step_time(P.t0, (long long)(P.kbase + k + 1), P.dt);
+                        ++n_reb;
+                        n_phase = 4;
+                    } else if (collide) {
+                        // inertial-frame elastic collision: |p| kept, B at R^{n+1}; new pitch
+                        // cosine from Eq. 10 (mu = 1 - 2a) or Eq. 12 (mu = +-sqrt(a))
+                        const uint4 wd = draw(id, P.seed, event++);
+                        if constexpr (sizeof(T) == 8) {
+                            const double a = u53(wd.x, wd.y);
+                            const double mu_new = (scatter_law == 0) ? 1.0 - 2.0 * a
+                                                                     : ((wd.x & 1u) ? -sqrt(a) : sqrt(a));
+                            const double Bm = (double)ax.Bm;
+                            const double uu = Acc::to(U);
+                            const double pm2 = uu * uu + 2.0 * (double)mub * Bm / P.m;
+                            const double pm = sqrt(pm2);
+                            U = mu_new * pm;
+                            mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
+                            if (P.collision_form == 0)
+                                S = -lambda * log(u53(wd.z, wd.w));
+                        } else {
+                            // sin^2 of the new pitch angle without cancellation: 4 a (1 - a)
+                            // for Eq. 10 (mu = (1 - a) - a), 1 - a for Eq. 12 (mu^2 = a)
+                            const UPair ua = u31(wd.x);
+                            float mu_new, sin2;
+                            if (scatter_law == 0) {
+                                mu_new = ua.ub - ua.u;
+                                sin2 = 4.0f * ua.u * ua.ub;
+                            } else {
+                                mu_new = (wd.x & 1u) ? -sqrtf(ua.u) : sqrtf(ua.u);
+                                sin2 = ua.ub;
+                            }
+                            const float Bm = (float)ax.Bm;
+                            const float uu = (float)Acc::val(U);
+                            const float pm2 = uu * uu + 2.0f * (float)mub * Bm * (float)ph.inv_m;
+                            U = df{mu_new * sqrtf(pm2), 0.0f};
+                            mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
+                            if (P.collision_form == 0)
+                                S = df{lambda_f * neg_log_u(u31(wd.z)), 0.0f};
+                        }
+                        ++ncoll;
+                        ++n_coll;
+                        n_phase = 4;
+                    } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    F1[c] = F0[c];
-                    F0[c] = F2[c];
+                        for (int c = 0; c < 4; ++c) {
+                            F1[c] = F0[c];
+                            F0[c] = Fo[c];
+                        }
+                        vpar0 = ax.vpar;
+                        Bm0 = ax.Bm;
+                    }
+                } else if (phase == 2) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        F0[c] = Fo[c];
+                    vpar0 = ax.vpar;
+                    Bm0 = ax.Bm;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        F1[c] = Fo[c];
                 }
-                vpar0 = ax2.vpar;
-                Bm0 = ax2.Bm;
             }
             hprev = dtT;
             if (!(m_finite(Acc::val(Rx)) && m_finite(Acc::val(U)) && m_finite(F0[0])))
@@ -271,8 +367,8 @@ __global__ void __launch_bounds__(256) push_kernel(const GridMeta<T> gm, const P
 
             if (k == next_tally) {
                 next_tally += P.tally.cadence;
-                const double t_new = P.t0 + (double)(P.kbase + k + 1) * P.dt;
-                tally_sample<T>(P.tally, P, e, Acc::val(Rx), Acc::val(Ry), Acc::val(Rz), Acc::val(U),
+                const double t_new = step_time(P.t0, (long long)(P.kbase + k + 1), P.dt);
+                tally_sample<T>(P.tally, P, ph, e, Acc::val(Rx), Acc::val(Ry), Acc::val(Rz), Acc::val(U),
                                 mub, Bm0, t_new - t_birth, ncoll,
                                 t_birth >= P.tally.t_start && (int)e < P.tally.n_ens);
             }
@@ -397,8 +493,10 @@ static Phys<T> make_phys(const PhysHost &p)
 {
     Phys<T> q;
     q.qm = (T)p.qm;
+    q.inv_qm = (T)(1.0 / p.qm);
     q.inv_m = (T)p.inv_m;
     q.inv_c2 = (T)p.inv_c2;
+    q.mc2 = (T)(1.0 / (p.inv_m * p.inv_c2));
     q.drift_mask = p.drift_mask;
     return q;
 }
