@@ -227,7 +227,7 @@ def main():
 
     import torch
 
-    from paper_2403_06706_gb300 import gcpush
+    from paper_2403_06706_gb300 import gcpush, shard
 
     torch.cuda.set_device(local)
     dist = None
@@ -247,7 +247,7 @@ def main():
 
     # ---------------- device-resident FP32 path ---------------------------------------
     ctx = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wl.seed,
-                         dt_init=wl.dt, id_base=rank * n_rank)
+                         dt_init=wl.dt, id_base=shard.id_base(rank, n_rank))
     ctx.field_load(nodes, wl.wind.r_min_au, wl.wind.r_max_au)
     ctx.inject(list(wl.ensembles))
     ctx.set_launch(**LAUNCH)
@@ -323,7 +323,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         c64 = gcpush.Context(precision=gcpush.PREC_FP64, device=local, stream=stream, seed=wl.seed,
-                             dt_init=wl.dt, id_base=rank * n_rank)
+                             dt_init=wl.dt, id_base=shard.id_base(rank, n_rank))
         c64.field_load(nodes, wl.wind.r_min_au, wl.wind.r_max_au)
         c64.inject(list(wl.ensembles))
         c64.set_launch(**LAUNCH)
