@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--particles", type=int, default=3_000_000,
                     help="particles per GPU (split over the three lambda ensembles); smaller "
                          "values are for profiler captures")
@@ -341,6 +342,35 @@ def main():
                 "note": "same workload, FP64 grid and arithmetic; timed after the same start-up"}
         c64.close()
 
+    # ---------------- 64 uneven ensembles, graph replay, autotuned launch shape -------------
+    batched = None
+    if not args.no_batched:
+        wb = synth.c3_batched()
+        cb = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wb.seed,
+                            dt_init=wb.dt, id_base=shard.id_base(rank, wb.n_particles))
+        cb.field_load(nodes, wb.wind.r_min_au, wb.wind.r_max_au)
+        cb.inject(list(wb.ensembles))
+        cb.tally_arm(**TALLY)
+        cb.advance(wb.dt, 1000)  # spread the ensembles out before tuning
+        choice = cb.autotune(wb.dt, trial_steps=200)
+        cb.set_graph(True)
+        nb_steps = 500
+        for _ in range(2):
+            cb.advance(wb.dt, nb_steps)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            cb.advance(wb.dt, nb_steps)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1)
+        batched = {"workload": wb.name, "ensembles": len(wb.ensembles), "particles": wb.n_particles,
+                   "value": world * wb.n_particles * nb_steps * args.steps / (bms / 1e3), "unit": UNIT,
+                   "push_steps_per_call": nb_steps, "graph": True, "autotune": choice}
+        cb.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, nodes)
@@ -354,7 +384,7 @@ def main():
             "config": config_dict(wl, n_rank),
             "parallelism": f"particles sharded by id, {world} GPU(s), no data-path collective",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clocks, "fp64_plain": fp64,
+            "clocks": clocks, "fp64_plain": fp64, "batched": batched,
             "accuracy": "FP32 path within 1e-4 of the FP64 oracle over the first 1e3 steps; "
                         "FP64 path within 1e-9 (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)",
         }

@@ -194,9 +194,30 @@ int gc_stats(gc_ctx *ctx, gc_stats_out *out);
  * checkpoint written with gc_particles_get; tally cadence and birth times follow them. */
 int gc_set_clock(gc_ctx *ctx, double t, int64_t step);
 
-/* Launch shape: threads per block (0 = default), steps per kernel launch (0 = default),
- * and the period of the cell sort in steps (0 = never). */
-int gc_set_launch(gc_ctx *ctx, int block, int steps_per_launch, int sort_every);
+/* Launch shape: threads per block (multiple of 32 up to 128; 0 = keep), steps per kernel
+ * launch (0 = keep), the period of the cell sort in steps (0 = never), and the grid in
+ * resident waves of blocks (k >= 1: k x SMs x resident blocks per SM, each thread walking
+ * several particles; 0: one thread per particle). */
+int gc_set_launch(gc_ctx *ctx, int block, int steps_per_launch, int sort_every, int grid_waves);
+
+/* Replay gc_advance from CUDA graphs (enable != 0). The first call of a given pattern
+ * (dt, n_steps, lambda, launch shape, tallies, buffers) captures its sorts and push
+ * launches into a graph on an internal stream; later calls with the same pattern replay
+ * it on the context's stream with the clock read from device memory. Results are those of
+ * the direct path. A context caches up to four graphs; reallocation drops them. */
+int gc_set_graph(gc_ctx *ctx, int enable);
+
+/* Result of gc_autotune. */
+typedef struct {
+    int32_t block, grid_waves, steps_per_launch, sort_every;
+    double particle_steps_per_s; /* measured rate of the chosen shape */
+    int32_t trials, pad0;
+} gc_launch_choice;
+
+/* Time trial_steps steps of dt for each launch shape of a small search space (block size,
+ * grid waves, cell-sort period) from a snapshot of the current state, keep the fastest
+ * with gc_set_launch, and restore the state, clock, counters and tallies as they were. */
+int gc_autotune(gc_ctx *ctx, double dt, int64_t trial_steps, gc_launch_choice *best);
 
 /* Sort the particles by grid cell now (results are unchanged: every random draw is keyed
  * by particle id and every tally is an integer sum). */

@@ -69,6 +69,42 @@ __global__ void convert_nodes(const float *src, double *dst, size_t n)
 const int kF64Fields = 13; // x y z u mub vpar s_rem h_prev t_birth u_inj mub_inj + F0, F1 rows
 const int kU32Fields = 5;
 
+// one timed interval (a push launch or a sort) bracketed by two events
+struct Timed {
+    cudaEvent_t a, b;
+    int kind; // 0 push, 1 sort
+};
+
+struct LaunchCounts {
+    uint64_t kernels = 0, pushes = 0, sorts = 0;
+};
+
+// A captured advance: valid for one call pattern and one pair of state buffers.
+struct GraphKey {
+    double dt, lambda_au;
+    int64_t n_steps, n, cap, steps_since_sort, n_ens;
+    int block, grid_waves, steps_per_launch, sort_every, tally_on;
+    const void *st_x, *alt_x, *tally, *grid, *ens;
+    bool operator==(const GraphKey &o) const
+    {
+        return dt == o.dt && lambda_au == o.lambda_au && n_steps == o.n_steps && n == o.n && cap == o.cap &&
+               steps_since_sort == o.steps_since_sort && n_ens == o.n_ens && block == o.block &&
+               grid_waves == o.grid_waves && steps_per_launch == o.steps_per_launch &&
+               sort_every == o.sort_every && tally_on == o.tally_on && st_x == o.st_x && alt_x == o.alt_x &&
+               tally == o.tally && grid == o.grid && ens == o.ens;
+    }
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Timed> timed; // events owned by this entry
+    LaunchCounts counts;
+    gcp::StateDev st_after{}, alt_after{};
+    int64_t steps_since_sort_after = 0;
+};
+
 } // namespace
 
 void gcp::set_last_error(const char *msg) { g_err = msg; }
@@ -115,10 +151,16 @@ struct gc_ctx {
 
     // instrumentation: CUDA events around push launches and sorts
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, int>> push_ev, sort_ev; // pending (start, stop) pool indices
+    std::vector<Timed> pending; // intervals recorded since the last harvest (pool events)
     size_t ev_next = 0;
     uint64_t kernel_launches = 0, push_launches = 0, sorts = 0;
     double push_ms = 0.0, sort_ms = 0.0;
+
+    // graph replay: clock words read by the push kernel, captured graphs
+    bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;
+    double *d_clock = nullptr, *h_clock = nullptr;
+    std::vector<GraphEntry *> graphs;
 
     // order of the particle slots
     bool in_id_order = true; // slot k holds the k-th smallest id
@@ -127,6 +169,8 @@ struct gc_ctx {
 
     // launch shape
     int block = 128;
+    int grid_waves = 1;      // resident waves of blocks (0: one thread per particle)
+    int blocks_per_sm[5] = {0, 0, 0, 0, 0}; // occupancy per block size / 32, cached
     int steps_per_launch = 2000;
     int sort_every = 0;
     int64_t steps_since_sort = 0;
@@ -167,10 +211,13 @@ void free_state(gcp::StateDev &s)
 }
 
 // Grow the particle arrays to hold `need` particles, keeping the first c->n.
+void drop_graphs(gc_ctx *c);
+
 int reserve(gc_ctx *c, int64_t need)
 {
     if (need <= c->cap)
         return GC_OK;
+    drop_graphs(c); // captured graphs hold the old buffers
     int64_t cap = std::max<int64_t>(need, c->cap + c->cap / 2);
     gcp::StateDev ns{};
     double **dd[] = {&ns.x, &ns.y, &ns.z, &ns.u, &ns.mub, &ns.vpar, &ns.s_rem, &ns.h_prev,
@@ -221,6 +268,7 @@ int reserve(gc_ctx *c, int64_t need)
 
 int upload_ensembles(gc_ctx *c)
 {
+    drop_graphs(c);
     if ((int64_t)c->ens.size() > c->ens_cap) {
         if (c->d_ens) cudaFree(c->d_ens);
         c->d_ens = nullptr;
@@ -232,7 +280,16 @@ int upload_ensembles(gc_ctx *c)
     return GC_OK;
 }
 
-void harvest_events(gc_ctx *c);
+// sum the device times of recorded intervals (their stream must be synchronised)
+void harvest(gc_ctx *c, const std::vector<Timed> &tl)
+{
+    for (const Timed &t : tl) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess)
+            (t.kind == 0 ? c->push_ms : c->sort_ms) += ms;
+    }
+    cudaGetLastError(); // a timing that could not be read is not an error of the next call
+}
 
 // read back the status words of the last launches (synchronises the stream)
 int collect_status(gc_ctx *c, bool *anomaly)
@@ -241,7 +298,9 @@ int collect_status(gc_ctx *c, bool *anomaly)
     CUDA_TRY(cudaMemcpyAsync(c->h_counters, c->d_counters, 2 * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    harvest_events(c);
+    harvest(c, c->pending);
+    c->pending.clear();
+    c->ev_next = 0;
     const uint32_t f = *c->h_flags;
     c->flags_or |= f;
     c->collisions += c->h_counters[0];
@@ -253,52 +312,257 @@ int collect_status(gc_ctx *c, bool *anomaly)
     return GC_OK;
 }
 
-int event_pair(gc_ctx *c, std::pair<int, int> *out)
+// Two events for one interval: from the context's pool (owned == nullptr, harvested by
+// collect_status) or created for, and owned by, a captured graph.
+int new_interval(gc_ctx *c, int kind, std::vector<Timed> *owned, Timed *out)
 {
+    out->kind = kind;
+    if (owned) {
+        CUDA_TRY(cudaEventCreate(&out->a));
+        CUDA_TRY(cudaEventCreate(&out->b));
+        owned->push_back(*out);
+        return GC_OK;
+    }
     while (c->ev_pool.size() < c->ev_next + 2) {
         cudaEvent_t e;
         CUDA_TRY(cudaEventCreate(&e));
         c->ev_pool.push_back(e);
     }
-    out->first = (int)c->ev_next;
-    out->second = (int)c->ev_next + 1;
+    out->a = c->ev_pool[c->ev_next];
+    out->b = c->ev_pool[c->ev_next + 1];
     c->ev_next += 2;
+    c->pending.push_back(*out);
     return GC_OK;
 }
 
-// sum the device times of the pending event pairs (the stream must be synchronised)
-void harvest_events(gc_ctx *c)
+int do_sort(gc_ctx *c, cudaStream_t s, std::vector<Timed> *owned, LaunchCounts *lc)
 {
-    for (auto &p : c->push_ev) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->ev_pool[p.first], c->ev_pool[p.second]) == cudaSuccess)
-            c->push_ms += ms;
-    }
-    for (auto &p : c->sort_ev) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->ev_pool[p.first], c->ev_pool[p.second]) == cudaSuccess)
-            c->sort_ms += ms;
-    }
-    c->push_ev.clear();
-    c->sort_ev.clear();
-    c->ev_next = 0;
-}
-
-int do_sort(gc_ctx *c)
-{
-    std::pair<int, int> ev;
-    TRY(event_pair(c, &ev));
-    CUDA_TRY(cudaEventRecord(c->ev_pool[ev.first], c->stream));
-    cudaError_t e = gcp::sort_by_cell(c->sortw, c->st, c->gh, (int)c->ens.size(), c->stream);
+    Timed t;
+    TRY(new_interval(c, 1, owned, &t));
+    CUDA_TRY(cudaEventRecord(t.a, s));
+    cudaError_t e = gcp::sort_by_cell(c->sortw, c->st, c->gh, (int)c->ens.size(), s);
     if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? GC_ERR_NOMEM : GC_ERR_CUDA, "cell sort: %s",
                     cudaGetErrorString(e));
-    CUDA_TRY(cudaEventRecord(c->ev_pool[ev.second], c->stream));
-    c->sort_ev.push_back(ev);
-    c->kernel_launches += gcp::kSortKernels;
-    c->sorts += 1;
+    CUDA_TRY(cudaEventRecord(t.b, s));
+    lc->kernels += gcp::kSortKernels;
+    lc->sorts += 1;
     c->steps_since_sort = 0;
     c->in_id_order = false;
+    return GC_OK;
+}
+
+int push_grid(gc_ctx *c)
+{
+    int &nb = c->blocks_per_sm[c->block / 32];
+    if (nb <= 0) {
+        nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block);
+        cudaGetLastError(); // an occupancy query failure only means "one block"
+        if (nb < 1) nb = 1;
+    }
+    const int64_t want = (c->n + c->block - 1) / c->block;
+    if (c->grid_waves <= 0)
+        return (int)std::min<int64_t>(want, 0x7FFFFFFF);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->grid_waves * c->sm_count * nb));
+}
+
+// Enqueue the launches of one advance on stream s: cell sorts on schedule and push
+// launches of at most steps_per_launch steps. clock_dev != nullptr makes the kernels take
+// the clock from device memory (graph capture).
+int enqueue_advance(gc_ctx *c, cudaStream_t s, double dt, int64_t n_steps, double lambda_au,
+                    const double *clock_dev, std::vector<Timed> *owned, LaunchCounts *lc)
+{
+    const int grid = push_grid(c);
+    gcp::PushParams P{};
+    P.st = c->st;
+    P.ens = c->d_ens;
+    P.dt = dt;
+    P.t0 = c->t;
+    P.collision_form = c->opt.collision_form;
+    P.no_scatter = c->opt.no_scatter;
+    P.no_rebirth = c->opt.no_rebirth;
+    P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
+    P.seed = c->opt.seed;
+    P.m = c->opt.mass;
+    P.c2 = kC * kC;
+    P.tally_on = c->tally_on ? 1 : 0;
+    P.tally = c->tdev;
+    P.gflags = c->d_flags;
+    P.counters = c->d_counters;
+    P.clock = clock_dev;
+    const gcp::PhysHost ph = c->phys();
+
+    int64_t done = 0;
+    while (done < n_steps) {
+        if (c->sort_every > 0 && c->steps_since_sort >= c->sort_every) {
+            TRY(do_sort(c, s, owned, lc));
+            P.st = c->st;
+        }
+        int64_t chunk = std::min<int64_t>(n_steps - done, c->steps_per_launch);
+        if (c->sort_every > 0)
+            chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, c->sort_every - c->steps_since_sort));
+        P.step0 = c->step + done;
+        P.kbase = done;
+        P.n_steps = (int32_t)chunk;
+        Timed t;
+        TRY(new_interval(c, 0, owned, &t));
+        CUDA_TRY(cudaEventRecord(t.a, s));
+        CUDA_TRY(gcp::launch_push(c->opt.precision, c->gh, ph, P, c->block, grid, s));
+        CUDA_TRY(cudaEventRecord(t.b, s));
+        lc->kernels += 1;
+        lc->pushes += 1;
+        done += chunk;
+        c->steps_since_sort += chunk;
+    }
+    return GC_OK;
+}
+
+void add_counts(gc_ctx *c, const LaunchCounts &lc)
+{
+    c->kernel_launches += lc.kernels;
+    c->push_launches += lc.pushes;
+    c->sorts += lc.sorts;
+}
+
+void free_graph(GraphEntry *g)
+{
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (const Timed &t : g->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    delete g;
+}
+
+void drop_graphs(gc_ctx *c)
+{
+    for (GraphEntry *g : c->graphs)
+        free_graph(g);
+    c->graphs.clear();
+}
+
+GraphKey graph_key(gc_ctx *c, double dt, int64_t n_steps, double lambda_au)
+{
+    GraphKey k{};
+    k.dt = dt;
+    k.lambda_au = lambda_au;
+    k.n_steps = n_steps;
+    k.n = c->n;
+    k.cap = c->cap;
+    k.steps_since_sort = c->steps_since_sort;
+    k.n_ens = (int64_t)c->ens.size();
+    k.block = c->block;
+    k.grid_waves = c->grid_waves;
+    k.steps_per_launch = c->steps_per_launch;
+    k.sort_every = c->sort_every;
+    k.tally_on = c->tally_on ? 1 : 0;
+    k.st_x = c->st.x;
+    k.alt_x = c->sortw.alt.x;
+    k.tally = c->d_tally;
+    k.grid = c->d_grid;
+    k.ens = c->d_ens;
+    return k;
+}
+
+// Capture the advance for this call pattern into a graph (once), then replay it. The
+// graph resets the status words, copies the clock from a pinned host word, runs the sorts
+// and push launches, and copies the status words back.
+int advance_graph(gc_ctx *c, double dt, int64_t n_steps, double lambda_au, bool *anomaly)
+{
+    const GraphKey key = graph_key(c, dt, n_steps, lambda_au);
+    GraphEntry *G = nullptr;
+    for (GraphEntry *g : c->graphs)
+        if (g->key == key) G = g;
+    if (!G) {
+        if (!c->cap_stream)
+            CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (!c->d_clock) {
+            CUDA_TRY(cudaMalloc(&c->d_clock, 2 * sizeof(double)));
+            CUDA_TRY(cudaMallocHost(&c->h_clock, 2 * sizeof(double)));
+        }
+        if (c->sort_every > 0) {
+            cudaError_t e = gcp::sort_reserve(c->sortw, c->st, c->gh);
+            if (e != cudaSuccess)
+                return fail(GC_ERR_NOMEM, "gc_advance: sort buffers: %s", cudaGetErrorString(e));
+        }
+        CUDA_TRY(gcp::preload_kernels());
+        CUDA_TRY(gcp::sort_preload());
+        push_grid(c); // occupancy query outside the capture
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        cudaGetLastError(); // start the capture with no stale error
+        G = new GraphEntry();
+        G->key = graph_key(c, dt, n_steps, lambda_au);
+        const gcp::StateDev st0 = c->st, alt0 = c->sortw.alt;
+        const int64_t ss0 = c->steps_since_sort;
+        const bool order0 = c->in_id_order;
+        cudaStream_t s = c->cap_stream;
+        int rc = GC_OK;
+        const char *what = "cudaStreamBeginCapture";
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            what = "status reset";
+            e = cudaMemsetAsync(c->d_flags, 0, sizeof(uint32_t), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), s);
+            if (e == cudaSuccess) {
+                what = "clock copy";
+                e = cudaMemcpyAsync(c->d_clock, c->h_clock, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+            }
+            if (e == cudaSuccess) {
+                what = "launches";
+                rc = enqueue_advance(c, s, dt, n_steps, lambda_au, c->d_clock, &G->timed, &G->counts);
+            }
+            if (e == cudaSuccess && rc == GC_OK) {
+                what = "status copy";
+                e = cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(c->h_counters, c->d_counters, 2 * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, s);
+            }
+            const cudaError_t e2 = cudaStreamEndCapture(s, &G->graph);
+            if (e == cudaSuccess && rc == GC_OK && e2 != cudaSuccess) {
+                e = e2;
+                what = "cudaStreamEndCapture";
+            }
+        }
+        G->st_after = c->st;
+        G->alt_after = c->sortw.alt;
+        G->steps_since_sort_after = c->steps_since_sort;
+        c->st = st0; // capture ran no work: the state is where it was
+        c->sortw.alt = alt0;
+        c->steps_since_sort = ss0;
+        c->in_id_order = order0;
+        if (e == cudaSuccess && rc == GC_OK) {
+            what = "cudaGraphInstantiate";
+            e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+        }
+        if (e != cudaSuccess || rc != GC_OK) {
+            free_graph(G);
+            cudaGetLastError();
+            if (rc != GC_OK) return rc;
+            return fail(GC_ERR_CUDA, "gc_advance: graph capture (%s): %s", what, cudaGetErrorString(e));
+        }
+        if (c->graphs.size() >= 4) {
+            free_graph(c->graphs.front());
+            c->graphs.erase(c->graphs.begin());
+        }
+        c->graphs.push_back(G);
+    }
+    c->h_clock[0] = c->t;
+    c->h_clock[1] = (double)c->step;
+    CUDA_TRY(cudaGraphLaunch(G->exec, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    harvest(c, G->timed);
+    add_counts(c, G->counts);
+    c->st = G->st_after;
+    c->sortw.alt = G->alt_after;
+    c->steps_since_sort = G->steps_since_sort_after;
+    if (G->counts.sorts) c->in_id_order = false;
+    const uint32_t f = *c->h_flags;
+    c->flags_or |= f;
+    c->collisions += c->h_counters[0];
+    c->rebirths += c->h_counters[1];
+    *anomaly = (f != 0);
     return GC_OK;
 }
 
@@ -377,6 +641,10 @@ void gc_destroy(gc_ctx *c)
     if (c->d_counters) cudaFree(c->d_counters);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->h_counters) cudaFreeHost(c->h_counters);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->d_clock) cudaFree(c->d_clock);
+    if (c->h_clock) cudaFreeHost(c->h_clock);
     gcp::sort_free(c->sortw);
     for (cudaEvent_t e : c->ev_pool)
         cudaEventDestroy(e);
@@ -401,6 +669,7 @@ int gc_field_load(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_o
     const bool want64 = (c->opt.precision == GC_PREC_FP64);
     const size_t esz = want64 ? sizeof(double) : sizeof(float);
     const size_t in_esz = (g->dtype == GC_DTYPE_F64) ? sizeof(double) : sizeof(float);
+    drop_graphs(c);
     if (c->d_grid) {
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         cudaFree(c->d_grid);
@@ -539,17 +808,18 @@ int gc_particles_inject(gc_ctx *c, const gc_ensemble_desc *e, int n_ens)
     return GC_OK;
 }
 
-int gc_set_launch(gc_ctx *c, int block, int steps_per_launch, int sort_every)
+int gc_set_launch(gc_ctx *c, int block, int steps_per_launch, int sort_every, int grid_waves)
 {
     if (!c)
         return fail(GC_ERR_INVALID, "gc_set_launch: null context");
-    if (block != 0 && (block < 32 || block > 256 || block % 32 != 0))
-        return fail(GC_ERR_INVALID, "gc_set_launch: block must be a multiple of 32 in [32, 256]");
-    if (steps_per_launch < 0 || sort_every < 0)
+    if (block != 0 && (block < 32 || block > 128 || block % 32 != 0))
+        return fail(GC_ERR_INVALID, "gc_set_launch: block must be a multiple of 32 in [32, 128]");
+    if (steps_per_launch < 0 || sort_every < 0 || grid_waves < 0)
         return fail(GC_ERR_INVALID, "gc_set_launch: negative argument");
     if (block) c->block = block;
     if (steps_per_launch) c->steps_per_launch = steps_per_launch;
     c->sort_every = sort_every;
+    c->grid_waves = grid_waves;
     return GC_OK;
 }
 
@@ -562,7 +832,9 @@ int gc_sort(gc_ctx *c)
     TRY(set_device(c));
     if (c->n < 2)
         return GC_OK;
-    TRY(do_sort(c));
+    LaunchCounts lc;
+    TRY(do_sort(c, c->stream, nullptr, &lc));
+    add_counts(c, lc);
     bool anomaly = false;
     return collect_status(c, &anomaly);
 }
@@ -581,59 +853,151 @@ int gc_advance(gc_ctx *c, double dt, int64_t n_steps, double lambda_au)
         c->step += n_steps;
         return GC_OK;
     }
-    int nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block);
-    if (nb < 1) nb = 1;
-    const int64_t want = (c->n + c->block - 1) / c->block;
-    const int grid = (int)std::min<int64_t>(want, (int64_t)c->sm_count * nb);
-
-    gcp::PushParams P{};
-    P.st = c->st;
-    P.ens = c->d_ens;
-    P.dt = dt;
-    P.t0 = c->t;
-    P.collision_form = c->opt.collision_form;
-    P.no_scatter = c->opt.no_scatter;
-    P.no_rebirth = c->opt.no_rebirth;
-    P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
-    P.seed = c->opt.seed;
-    P.m = c->opt.mass;
-    P.c2 = kC * kC;
-    P.tally_on = c->tally_on ? 1 : 0;
-    P.tally = c->tdev;
-    P.gflags = c->d_flags;
-    P.counters = c->d_counters;
-    const gcp::PhysHost ph = c->phys();
-
-    int64_t done = 0;
-    while (done < n_steps) {
-        if (c->sort_every > 0 && c->steps_since_sort >= c->sort_every) {
-            TRY(do_sort(c));
-            P.st = c->st;
-        }
-        int64_t chunk = std::min<int64_t>(n_steps - done, c->steps_per_launch);
-        if (c->sort_every > 0)
-            chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, c->sort_every - c->steps_since_sort));
-        P.step0 = c->step + done;
-        P.kbase = done;
-        P.n_steps = (int32_t)chunk;
-        std::pair<int, int> ev;
-        TRY(event_pair(c, &ev));
-        CUDA_TRY(cudaEventRecord(c->ev_pool[ev.first], c->stream));
-        CUDA_TRY(gcp::launch_push(c->opt.precision, c->gh, ph, P, c->block, grid, c->stream));
-        CUDA_TRY(cudaEventRecord(c->ev_pool[ev.second], c->stream));
-        c->push_ev.push_back(ev);
-        c->kernel_launches += 1;
-        c->push_launches += 1;
-        done += chunk;
-        c->steps_since_sort += chunk;
+    bool anomaly = false;
+    if (c->use_graph) {
+        TRY(advance_graph(c, dt, n_steps, lambda_au, &anomaly));
+    } else {
+        LaunchCounts lc;
+        TRY(enqueue_advance(c, c->stream, dt, n_steps, lambda_au, nullptr, nullptr, &lc));
+        add_counts(c, lc);
+        TRY(collect_status(c, &anomaly));
     }
     c->t += (double)n_steps * dt;
     c->step += n_steps;
     c->particle_steps += (uint64_t)c->n * (uint64_t)n_steps;
-    bool anomaly = false;
-    TRY(collect_status(c, &anomaly));
     if (anomaly)
         return fail(GC_ERR_DEVICE_ANOMALY, "gc_advance: particles flagged (0x%x)", c->flags_or);
+    return GC_OK;
+}
+
+int gc_set_graph(gc_ctx *c, int enable)
+{
+    if (!c)
+        return fail(GC_ERR_INVALID, "gc_set_graph: null context");
+    TRY(set_device(c));
+    c->use_graph = enable != 0;
+    if (!c->use_graph) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+    }
+    return GC_OK;
+}
+
+namespace {
+
+// D2D copy of n particles between two state buffers of equal capacity
+int copy_state(const gcp::StateDev &dst, const gcp::StateDev &src, int64_t n, int64_t cap, cudaStream_t s)
+{
+    double *const dd[] = {dst.x, dst.y, dst.z, dst.u, dst.mub, dst.vpar, dst.s_rem, dst.h_prev,
+                          dst.t_birth, dst.u_inj, dst.mub_inj};
+    const double *const sd[] = {src.x, src.y, src.z, src.u, src.mub, src.vpar, src.s_rem, src.h_prev,
+                                src.t_birth, src.u_inj, src.mub_inj};
+    for (int k = 0; k < 11; ++k)
+        CUDA_TRY(cudaMemcpyAsync(dd[k], sd[k], (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dst.F0, src.F0, (size_t)cap * 32, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dst.F1, src.F1, (size_t)cap * 32, cudaMemcpyDeviceToDevice, s));
+    uint32_t *const du[] = {dst.id, dst.ens, dst.event, dst.ncoll, dst.flags};
+    const uint32_t *const su[] = {src.id, src.ens, src.event, src.ncoll, src.flags};
+    for (int k = 0; k < kU32Fields; ++k)
+        CUDA_TRY(cudaMemcpyAsync(du[k], su[k], (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    return GC_OK;
+}
+
+} // namespace
+
+int gc_autotune(gc_ctx *c, double dt, int64_t trial_steps, gc_launch_choice *best)
+{
+    if (!c || !(dt > 0.0) || trial_steps < 1)
+        return fail(GC_ERR_INVALID, "gc_autotune: need a context, dt > 0 and trial_steps >= 1");
+    if (!c->has_field || c->n == 0)
+        return fail(GC_ERR_STATE, "gc_autotune: needs a field and particles");
+    TRY(set_device(c));
+    // snapshot of the state; every trial starts from it and the state is restored after
+    gcp::StateDev bk{};
+    {
+        cudaError_t e = gcp::alloc_state(bk, c->cap);
+        if (e != cudaSuccess) {
+            gcp::free_state_arrays(bk);
+            return fail(GC_ERR_NOMEM, "gc_autotune: snapshot: %s", cudaGetErrorString(e));
+        }
+    }
+    int rc = copy_state(bk, c->st, c->n, c->cap, c->stream);
+    const double t_sv = c->t;
+    const int64_t step_sv = c->step, ss_sv = c->steps_since_sort;
+    const uint64_t coll_sv = c->collisions, reb_sv = c->rebirths, ps_sv = c->particle_steps;
+    const uint32_t flags_sv = c->flags_or;
+    const bool tally_sv = c->tally_on, graph_sv = c->use_graph, order_sv = c->in_id_order;
+    const int blk_sv = c->block, waves_sv = c->grid_waves, spl_sv = c->steps_per_launch, se_sv = c->sort_every;
+    c->tally_on = false;
+    c->use_graph = false;
+    gc_launch_choice b{};
+    b.particle_steps_per_s = -1.0;
+    int trials = 0;
+    const int blocks[] = {64, 128};
+    const int waves[] = {1, 2, 4, 0};
+    const int sorts[] = {0, 250, 1000};
+    for (int blk : blocks) {
+        for (int wv : waves) {
+            for (int se : sorts) {
+                if (rc != GC_OK) break;
+                c->block = blk;
+                c->grid_waves = wv;
+                c->sort_every = se;
+                c->steps_per_launch = (int)std::min<int64_t>(trial_steps, 2000);
+                c->steps_since_sort = se; // a trial with sorting starts with one sort
+                rc = copy_state(c->st, bk, c->n, c->cap, c->stream);
+                if (rc != GC_OK) break;
+                const double push0 = c->push_ms, sort0 = c->sort_ms;
+                LaunchCounts lc;
+                rc = enqueue_advance(c, c->stream, dt, trial_steps, 0.0, nullptr, nullptr, &lc);
+                if (rc != GC_OK) break;
+                add_counts(c, lc);
+                bool an = false;
+                rc = collect_status(c, &an);
+                if (rc != GC_OK) break;
+                const double push_s = (c->push_ms - push0) * 1e-3;
+                const double sort_s = (c->sort_ms - sort0) * 1e-3;
+                // a sort serves sort_every steps: charge its share to this trial
+                const double per_step = push_s / trial_steps + (se > 0 ? sort_s / se : 0.0);
+                const double rate = (double)c->n / per_step;
+                ++trials;
+                if (rate > b.particle_steps_per_s) {
+                    b.block = blk;
+                    b.grid_waves = wv;
+                    b.sort_every = se;
+                    b.steps_per_launch = 2000;
+                    b.particle_steps_per_s = rate;
+                }
+            }
+        }
+    }
+    if (rc == GC_OK)
+        rc = copy_state(c->st, bk, c->n, c->cap, c->stream);
+    cudaStreamSynchronize(c->stream);
+    gcp::free_state_arrays(bk);
+    c->t = t_sv;
+    c->step = step_sv;
+    c->steps_since_sort = ss_sv;
+    c->collisions = coll_sv;
+    c->rebirths = reb_sv;
+    c->particle_steps = ps_sv;
+    c->flags_or = flags_sv;
+    c->tally_on = tally_sv;
+    c->use_graph = graph_sv;
+    c->in_id_order = order_sv;
+    if (rc != GC_OK) {
+        c->block = blk_sv;
+        c->grid_waves = waves_sv;
+        c->steps_per_launch = spl_sv;
+        c->sort_every = se_sv;
+        return rc;
+    }
+    c->block = b.block;
+    c->grid_waves = b.grid_waves;
+    c->steps_per_launch = b.steps_per_launch;
+    c->sort_every = b.sort_every;
+    b.trials = trials;
+    if (best) *best = b;
     return GC_OK;
 }
 
@@ -676,6 +1040,7 @@ int gc_tally(gc_ctx *c, const gc_tally_desc *arm, gc_tally_out *out)
         if ((double)ne * t.n_mu * t.n_E * t.n_r >= 2147483647.0 || (double)ne * t.n_age * t.n_E >= 2147483647.0)
             return fail(GC_ERR_INVALID, "gc_tally: histogram larger than 2^31 bins");
         CUDA_TRY(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
         free_tally(c);
         c->off_age = align_up(b_mer, 256);
         c->off_pad = align_up(c->off_age + b_age, 256);

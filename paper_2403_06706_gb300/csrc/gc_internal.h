@@ -51,6 +51,9 @@ struct PushParams {
     TallyDev tally;
     uint32_t *gflags;              // OR of particle flags raised in this launch
     unsigned long long *counters;  // [0] collisions, [1] rebirths
+    // optional clock in device memory ([0] time, [1] global step of the call's start); when
+    // set it replaces t0 and step0 - kbase, so a captured graph replays at any time
+    const double *clock;
 };
 
 struct InjectParams {
@@ -83,6 +86,8 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
 cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
                           const InjectParams &p, cudaStream_t s);
 int push_max_blocks_per_sm(int precision, int block);
+// load the push kernels now (a launch inside a stream capture must not trigger loading)
+cudaError_t preload_kernels();
 // message returned by gc_last_error() on the calling thread (gc_api.cu)
 void set_last_error(const char *msg);
 } // namespace gcp

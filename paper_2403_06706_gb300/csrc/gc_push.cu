@@ -172,6 +172,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned n_coll = 0, n_reb = 0;
     const T dtT = (T)P.dt;
+    double t0 = P.t0;
+    int64_t step0 = P.step0;
+    if (P.clock) {
+        t0 = P.clock[0];
+        step0 = (int64_t)P.clock[1] + P.kbase;
+    }
     // Eq. 5-6 weights at tau = 1: 3/2, -1/2 (AB2) and 2/3, 5/12, -1/12 (AM3)
     const T a0_1 = dtT * T(1.5), a1_1 = dtT * T(-0.5);
     const T c0_1 = dtT * T(2.0 / 3.0), cs_1 = dtT * T(5.0 / 12.0), c1_1 = dtT * T(-1.0 / 12.0);
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
         int next_tally = -1;
         if (P.tally_on) {
             const int64_t K = P.tally.cadence;
-            next_tally = (int)((K - 1 - (P.step0 % K)) % K);
+            next_tally = (int)((K - 1 - (step0 % K)) % K);
         }
 
         for (int k = 0; k < P.n_steps; ++k) {
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
                         U = Acc::from(P.st.u_inj[i]);
                         mub = (T)P.st.mub_inj[i];
                         ncoll = 0;
-                        t_birth = step_time(P.t0, (long long)(P.kbase + k + 1), P.dt);
+                        t_birth = step_time(t0, (long long)(P.kbase + k + 1), P.dt);
                         ++n_reb;
                         n_phase = 4;
                     } else if (collide) {
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
 
             if (k == next_tally) {
                 next_tally += P.tally.cadence;
-                const double t_new = step_time(P.t0, (long long)(P.kbase + k + 1), P.dt);
+                const double t_new = step_time(t0, (long long)(P.kbase + k + 1), P.dt);
                 tally_sample<T>(P.tally, P, ph, e, Acc::val(Rx), Acc::val(Ry), Acc::val(Rz), Acc::val(U),
                                 mub, Bm0, t_new - t_birth, ncoll,
                                 t_birth >= P.tally.t_start && (int)e < P.tally.n_ens);
@@ -504,6 +510,7 @@ static Phys<T> make_phys(const PhysHost &p)
 cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, const PushParams &p,
                         int block, int grid, cudaStream_t s)
 {
+    cudaGetLastError(); // report this launch only
     if (precision == 0)
         push_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
     else
@@ -523,6 +530,14 @@ cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
     else
         inject_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
     return cudaGetLastError();
+}
+
+cudaError_t preload_kernels()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, push_kernel<float>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<double>);
+    return e;
 }
 
 int push_max_blocks_per_sm(int precision, int block)

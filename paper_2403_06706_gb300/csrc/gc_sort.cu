@@ -198,11 +198,9 @@ cudaError_t unpermute_to_alt(SortWork &w, const StateDev &st, uint32_t id_lo, cu
     return cudaGetLastError();
 }
 
-cudaError_t sort_by_cell(SortWork &w, StateDev &st, const GridHost &g, int n_ens, cudaStream_t s)
+namespace {
+KeyGeom key_geom(const GridHost &g, int64_t *nbins)
 {
-    (void)n_ens;
-    const int64_t n = st.n;
-    if (n < 2) return cudaSuccess;
     KeyGeom kg;
     kg.r_min = g.r_min;
     kg.inv_dr = 1.0 / g.dr;
@@ -219,17 +217,55 @@ cudaError_t sort_by_cell(SortWork &w, StateDev &st, const GridHost &g, int n_ens
     kg.nr_c = ((g.n_r - 1) >> kg.shift) + 1;
     kg.nth_c = ((g.n_th - 1) >> kg.shift) + 1;
     kg.nph_c = ((g.n_ph - 1) >> kg.shift) + 1;
-    const int64_t nb = bins(kg.shift);
+    *nbins = bins(kg.shift);
+    return kg;
+}
 
+cudaError_t ensure_hist(SortWork &w, int64_t nb)
+{
+    if (w.nbins_cap >= nb) return cudaSuccess;
+    if (w.hist) cudaFree(w.hist);
+    w.hist = nullptr;
+    w.nbins_cap = 0;
+    const cudaError_t e = cudaMalloc(&w.hist, (size_t)nb * 4);
+    if (e == cudaSuccess) w.nbins_cap = nb;
+    return e;
+}
+} // namespace
+
+cudaError_t alloc_state(StateDev &s, int64_t cap) { return alloc_alt(s, cap); }
+
+cudaError_t sort_preload()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, key_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, scan_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, scatter_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, unpermute_kernel);
+    return e;
+}
+void free_state_arrays(StateDev &s) { free_alt(s); }
+
+cudaError_t sort_reserve(SortWork &w, const StateDev &st, const GridHost &g)
+{
+    int64_t nb = 0;
+    key_geom(g, &nb);
+    cudaError_t e = ensure_alt(w, st.cap);
+    if (e != cudaSuccess) return e;
+    return ensure_hist(w, nb);
+}
+
+cudaError_t sort_by_cell(SortWork &w, StateDev &st, const GridHost &g, int n_ens, cudaStream_t s)
+{
+    (void)n_ens;
+    const int64_t n = st.n;
+    if (n < 2) return cudaSuccess;
+    cudaGetLastError(); // report this sort's errors only
+    int64_t nb = 0;
+    const KeyGeom kg = key_geom(g, &nb);
     cudaError_t e;
     if ((e = ensure_alt(w, st.cap)) != cudaSuccess) return e;
-    if (w.nbins_cap < nb) {
-        if (w.hist) cudaFree(w.hist);
-        w.hist = nullptr;
-        w.nbins_cap = 0;
-        if ((e = cudaMalloc(&w.hist, (size_t)nb * 4)) != cudaSuccess) return e;
-        w.nbins_cap = nb;
-    }
+    if ((e = ensure_hist(w, nb)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.hist, 0, (size_t)nb * 4, s)) != cudaSuccess) return e;
     const int grid = grid_for(n, 256);
     key_kernel<<<grid, 256, 0, s>>>(st.x, st.y, st.z, n, kg, w.key, w.rank, w.hist);

@@ -25,6 +25,14 @@ cudaError_t sort_by_cell(SortWork &w, StateDev &st, const GridHost &g, int n_ens
 // [id_lo, id_lo + n)). Used to return the state in id order after cell sorts.
 cudaError_t unpermute_to_alt(SortWork &w, const StateDev &st, uint32_t id_lo, cudaStream_t s);
 void sort_free(SortWork &w);
+// Allocate the sort's buffers for st and grid g now (before a graph capture, which cannot
+// allocate).
+cudaError_t sort_reserve(SortWork &w, const StateDev &st, const GridHost &g);
+// load the sort kernels now (see preload_kernels)
+cudaError_t sort_preload();
+// A full set of state arrays of capacity cap (F0/F1 as [4][cap]) and its release.
+cudaError_t alloc_state(StateDev &s, int64_t cap);
+void free_state_arrays(StateDev &s);
 // kernels launched by one sort_by_cell / unpermute_to_alt call
 constexpr int kSortKernels = 3;
 constexpr int kUnpermuteKernels = 1;

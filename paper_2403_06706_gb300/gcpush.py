@@ -127,9 +127,16 @@ class StatsOut(C.Structure):
                 ("push_ms", C.c_double), ("sorts", C.c_uint64), ("sort_ms", C.c_double)]
 
 
+class LaunchChoice(C.Structure):
+    _fields_ = [("block", C.c_int32), ("grid_waves", C.c_int32), ("steps_per_launch", C.c_int32),
+                ("sort_every", C.c_int32), ("particle_steps_per_s", C.c_double),
+                ("trials", C.c_int32), ("pad0", C.c_int32)]
+
+
 EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_particles_inject",
            "gc_advance", "gc_tally", "gc_particles_get", "gc_particles_set", "gc_stats",
-           "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc")
+           "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc",
+           "gc_set_graph", "gc_autotune")
 
 _lib = None
 
@@ -156,7 +163,9 @@ def load(path: str | None = None):
         "gc_particles_get": (C.c_int, [vp, C.POINTER(ParticleSoA)]),
         "gc_particles_set": (C.c_int, [vp, C.POINTER(ParticleSoA)]),
         "gc_stats": (C.c_int, [vp, C.POINTER(StatsOut)]),
-        "gc_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "gc_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "gc_set_graph": (C.c_int, [vp, C.c_int]),
+        "gc_autotune": (C.c_int, [vp, C.c_double, C.c_int64, C.POINTER(LaunchChoice)]),
         "gc_sort": (C.c_int, [vp]),
         "gc_version": (C.c_int, []),
         "gc_set_clock": (C.c_int, [vp, C.c_double, C.c_int64]),
@@ -271,8 +280,18 @@ class Context:
     def advance(self, dt: float, n_steps: int, lambda_au: float = 0.0):
         _check(load().gc_advance(self._h, dt, int(n_steps), lambda_au), "gc_advance")
 
-    def set_launch(self, block: int = 0, steps_per_launch: int = 0, sort_every: int = 0):
-        _check(load().gc_set_launch(self._h, block, steps_per_launch, sort_every), "gc_set_launch")
+    def set_launch(self, block: int = 0, steps_per_launch: int = 0, sort_every: int = 0,
+                   grid_waves: int = 1):
+        _check(load().gc_set_launch(self._h, block, steps_per_launch, sort_every, grid_waves),
+               "gc_set_launch")
+
+    def set_graph(self, enable: bool = True):
+        _check(load().gc_set_graph(self._h, int(enable)), "gc_set_graph")
+
+    def autotune(self, dt: float, trial_steps: int = 200) -> dict:
+        b = LaunchChoice()
+        _check(load().gc_autotune(self._h, dt, int(trial_steps), C.byref(b)), "gc_autotune")
+        return {k: getattr(b, k) for k, _ in LaunchChoice._fields_ if k != "pad0"}
 
     def sort(self):
         _check(load().gc_sort(self._h), "gc_sort")
