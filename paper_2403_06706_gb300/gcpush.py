@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libgcpush.so")
-SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu", "gc_noalloc.cu")
+SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu", "gc_noalloc.cu", "gc_siren.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
@@ -136,7 +136,7 @@ class LaunchChoice(C.Structure):
 EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_particles_inject",
            "gc_advance", "gc_tally", "gc_particles_get", "gc_particles_set", "gc_stats",
            "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc",
-           "gc_set_graph", "gc_autotune")
+           "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn")
 
 _lib = None
 
@@ -165,6 +165,7 @@ def load(path: str | None = None):
         "gc_stats": (C.c_int, [vp, C.POINTER(StatsOut)]),
         "gc_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
         "gc_set_graph": (C.c_int, [vp, C.c_int]),
+        "gc_gemm_bf16_tn": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
         "gc_autotune": (C.c_int, [vp, C.c_double, C.c_int64, C.POINTER(LaunchChoice)]),
         "gc_sort": (C.c_int, [vp]),
         "gc_version": (C.c_int, []),
@@ -378,6 +379,15 @@ def state_buffers(n: int, alloc=np.zeros) -> dict:
 
 def state_nbytes(a: dict) -> int:
     return int(sum(v.nbytes for v in a.values()))
+
+
+def gemm_bf16_tn(A, B, C, split_k: int = 1, accumulate: bool = False, stream=None):
+    """C = A B^T (or C += A B^T) on the tensor cores; torch CUDA tensors (A, B bf16)."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert B.shape[1] == K and C.shape == (M, N) and A.is_contiguous() and B.is_contiguous()
+    _check(load().gc_gemm_bf16_tn(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, split_k,
+                                  int(accumulate), _stream_ptr(stream)), "gc_gemm_bf16_tn")
 
 
 def _stream_ptr(stream):
