@@ -219,3 +219,33 @@ def c5_large(n: int = 30_000_000) -> Workload:
     e = EnsembleSpec(n, lam_au=0.3, energy_law=1, E_lo_keV=20, E_hi_keV=500, E_index=3.0,
                      r_out_au=r_out_default(w))
     return Workload("parker512x256x512_eps0.2_16modes_3e7e", w, (e,), 0.5, 691200, "f32")
+
+
+# --------------------------------------------------------------------------------------
+# Neural-field inputs: the network's initial weights (seeded draws of the method, handed to
+# both the CUDA path and the oracle) and the scaling that makes the targets O(1).
+
+SIREN_HIDDEN = 256
+SIREN_OMEGA0 = 30.0
+
+
+def siren_init(seed: int = 0, n_h: int = SIREN_HIDDEN, n_out: int = 8, omega0: float = SIREN_OMEGA0):
+    """Flat float32 parameters in the order W1 (n_h x 3), b1, W2..W4 (n_h x n_h), b2..b4,
+    W5 (n_out x n_h), b5, initialised as in Sitzmann et al. (2020): first layer
+    U(-1/3, 1/3) (fan-in 3, its sine carries the frequency omega0); hidden layers with the
+    frequency folded in, U(-sqrt(6/n_h), sqrt(6/n_h)); linear output layer
+    U(-sqrt(6/n_h)/omega0, sqrt(6/n_h)/omega0); biases U(-1/sqrt(fan_in), 1/sqrt(fan_in))."""
+    rng = np.random.default_rng(seed + 1000)
+    parts = [rng.uniform(-1.0 / 3.0, 1.0 / 3.0, (n_h, 3)), rng.uniform(-1 / np.sqrt(3), 1 / np.sqrt(3), n_h)]
+    lim = np.sqrt(6.0 / n_h)
+    for _ in range(3):
+        parts += [rng.uniform(-lim, lim, (n_h, n_h)), rng.uniform(-1 / np.sqrt(n_h), 1 / np.sqrt(n_h), n_h)]
+    parts += [rng.uniform(-lim / omega0, lim / omega0, (n_out, n_h)),
+              rng.uniform(-1 / np.sqrt(n_h), 1 / np.sqrt(n_h), n_out)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def field_scales(w: WindSpec) -> dict:
+    """Scaling of the network's inputs and outputs: x = R / r_max; outputs are
+    B (r / 1 AU)^2 / B1, E (r / 1 AU) / (B1 u_sw), |B| (r / 1 AU)^2 / B1 and Phi / (B1 u_sw AU)."""
+    return {"r_scale": w.r_max_au * AU, "B_scale": w.B1, "E_scale": w.B1 * w.u_sw}
