@@ -44,9 +44,11 @@ UNIT = "particle-steps/s"
 FLOP_PER_PSTEP = 2 * (236 + 319) + 121
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM traffic of one push launch of this workload (ncu, profiles/push_fp32_c2.md); None
-# until captured for the current kernel
-PUSH_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one push launch of the default workload (3x10^6 particles,
+# 1000 steps per launch), from one ncu capture of the current kernel
+# (profiles/push_kernel_fp32_parker256_3e6.md); reported only for that launch shape
+PUSH_TRAFFIC_BYTES = 492_170_000 + 373_810_000
+PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
 
@@ -281,7 +283,8 @@ def main():
     achieved = FLOP_PER_PSTEP * n_rank * steps_per_launch / (push_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": PUSH_TRAFFIC_BYTES,
+                "traffic": (PUSH_TRAFFIC_BYTES if (n_rank, round(steps_per_launch)) == PUSH_TRAFFIC_SHAPE
+                            else None),
                 "kernel": "push_kernel<float>", "launch_ms": push_ms,
                 "flop_per_particle_step": FLOP_PER_PSTEP,
                 "peak_basis": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)",
