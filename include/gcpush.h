@@ -234,6 +234,14 @@ int gc_version(void);
 int gc_gemm_bf16_tn(const void *A, const void *B, float *C, int M, int N, int K, int split_k, int accumulate,
                     void *stream);
 
+/* The same GEMM with either operand stored MN-major: a_mn = 1 means A is given as its
+ * transpose (row-major K x M, M contiguous), b_mn = 1 that B is row-major K x N. This is how
+ * the training's backward products read activations and gradients without transposing
+ * them: dW = dZ^T H (both MN-major) and dH = dZ W (B MN-major). Same rules and errors as
+ * gc_gemm_bf16_tn, plus GC_ERR_INVALID for a_mn or b_mn outside {0, 1}. */
+int gc_gemm_bf16(const void *A, int a_mn, const void *B, int b_mn, float *C, int M, int N, int K, int split_k,
+                 int accumulate, void *stream);
+
 /* Device memory gc_advance_noalloc keeps for its own use on every GPU that loads the
  * library (held until the process exits), and the most ensembles it accepts. */
 #define GC_NOALLOC_SCRATCH_BYTES 40960

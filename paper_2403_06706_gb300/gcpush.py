@@ -136,7 +136,7 @@ class LaunchChoice(C.Structure):
 EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_particles_inject",
            "gc_advance", "gc_tally", "gc_particles_get", "gc_particles_set", "gc_stats",
            "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc",
-           "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn")
+           "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn", "gc_gemm_bf16")
 
 _lib = None
 
@@ -166,6 +166,8 @@ def load(path: str | None = None):
         "gc_set_launch": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
         "gc_set_graph": (C.c_int, [vp, C.c_int]),
         "gc_gemm_bf16_tn": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]),
+        "gc_gemm_bf16": (C.c_int, [vp, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   vp]),
         "gc_autotune": (C.c_int, [vp, C.c_double, C.c_int64, C.POINTER(LaunchChoice)]),
         "gc_sort": (C.c_int, [vp]),
         "gc_version": (C.c_int, []),
@@ -388,6 +390,17 @@ def gemm_bf16_tn(A, B, C, split_k: int = 1, accumulate: bool = False, stream=Non
     assert B.shape[1] == K and C.shape == (M, N) and A.is_contiguous() and B.is_contiguous()
     _check(load().gc_gemm_bf16_tn(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, split_k,
                                   int(accumulate), _stream_ptr(stream)), "gc_gemm_bf16_tn")
+
+
+def gemm_bf16(A, B, C, a_mn: bool = False, b_mn: bool = False, split_k: int = 1, accumulate: bool = False,
+              stream=None):
+    """C = op(A) op(B)^T on the tensor cores: op(A) is A (M x K) or, with a_mn, A^T for A
+    given as K x M; op(B) likewise N x K or K x N. torch CUDA tensors (A, B bf16, C fp32)."""
+    M, K = (A.shape[1], A.shape[0]) if a_mn else A.shape
+    N, Kb = (B.shape[1], B.shape[0]) if b_mn else B.shape
+    assert Kb == K and C.shape == (M, N) and A.is_contiguous() and B.is_contiguous()
+    _check(load().gc_gemm_bf16(A.data_ptr(), int(a_mn), B.data_ptr(), int(b_mn), C.data_ptr(), M, N, K, split_k,
+                               int(accumulate), _stream_ptr(stream)), "gc_gemm_bf16")
 
 
 def _stream_ptr(stream):

@@ -45,3 +45,30 @@ def test_gemm_rejects_bad_shapes():
     C = torch.zeros(100, 128, device="cuda")
     with pytest.raises(gcpush.GcError):
         gcpush.gemm_bf16_tn(A, B, C)
+
+
+@pytest.mark.parametrize("a_mn,b_mn", [(0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 128), (256, 128, 320)])
+def test_gemm_mn_major_operands(a_mn, b_mn, M, N, K):
+    """Operands stored transposed (MN-major shared-memory layout through TMA)."""
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 5 * K + 11 * a_mn + 13 * b_mn)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.zeros(M, N, device="cuda")
+    gcpush.gemm_bf16(A.t().contiguous() if a_mn else A, B.t().contiguous() if b_mn else B, C,
+                     a_mn=bool(a_mn), b_mn=bool(b_mn))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(C.cpu().numpy(), _ref(A, B), rtol=0, atol=1e-4 * np.sqrt(K))
+
+
+def test_gemm_mn_major_split_k():
+    """dW = dZ^T H shape of the training: both operands MN-major, K = batch, split over CTAs."""
+    M, N, K = 256, 256, 4096
+    g = torch.Generator(device="cuda").manual_seed(5)
+    dZ = torch.randn(K, M, device="cuda", generator=g).to(torch.bfloat16)
+    H = torch.randn(K, N, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.zeros(M, N, device="cuda")
+    gcpush.gemm_bf16(dZ, H, C, a_mn=True, b_mn=True, split_k=8, accumulate=True)
+    torch.cuda.synchronize()
+    ref = dZ.double().cpu().numpy().T @ H.double().cpu().numpy()
+    np.testing.assert_allclose(C.cpu().numpy(), ref, rtol=0, atol=2e-4 * np.sqrt(K))
