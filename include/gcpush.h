@@ -242,6 +242,75 @@ int gc_gemm_bf16_tn(const void *A, const void *B, float *C, int M, int N, int K,
 int gc_gemm_bf16(const void *A, int a_mn, const void *B, int b_mn, float *C, int M, int N, int K, int split_k,
                  int accumulate, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Neural field (north of the grid: an alternative field source). A SIREN (sine-activated
+ * MLP, Sitzmann et al. 2020) 3 -> 256 -> 256 -> 256 -> 256 -> 8 maps x = R / r_max to the
+ * grid's eight channels [B, E, |B|, Phi] scaled to O(1):
+ *   y_B = B (r / 1 AU)^2 / B_scale, y_E = E (r / 1 AU) / E_scale,
+ *   y_|B| = |B| (r / 1 AU)^2 / B_scale, y_Phi = Phi / (E_scale 1 AU).
+ * Layers: z1 = w0 (W1 x + b1), h_k = sin z_k, z_k = W_k h_{k-1} + b_k, y = W5 h4 + b5.
+ * Parameters are FP32 (GC_SIREN_NPARAMS floats, in this order: W1 [256][3], b1 [256],
+ * W2 [256][256] ([out][in]), b2, W3, b3, W4, b4, W5 [8][256], b5 [8]). Evaluation and
+ * training use BF16 copies of W2..W5 and BF16 activations with FP32 accumulation on the
+ * tensor cores; W1 and the biases stay FP32. The field's derivatives come from the
+ * network's exact Jacobian (three forward-mode tangents). */
+#define GC_SIREN_NPARAMS 200456
+enum { GC_FIELD_GRID = 0, GC_FIELD_SIREN = 1 };
+
+typedef struct {
+    double omega0;   /* frequency of the first layer's sine (30 in Sitzmann et al.) */
+    double r_max_au; /* input scaling x = R / r_max */
+    double B_scale;  /* T */
+    double E_scale;  /* V/m */
+} gc_siren_desc;
+
+/* Define the network and load its parameters (host or device FP32 array of
+ * GC_SIREN_NPARAMS); resets the Adam moments. */
+int gc_siren_set(gc_ctx *ctx, const gc_siren_desc *d, const float *params, int params_on_device);
+
+/* Copy the current FP32 parameters to a caller-owned host array of GC_SIREN_NPARAMS. */
+int gc_siren_get(gc_ctx *ctx, float *params_host);
+
+/* Raw network outputs at n points: x_dev (n x 3 FP32, device, already scaled), y_dev
+ * (n x 8) and, if J_dev is not NULL, J_dev (n x 8 x 3, dy_o / dx_j). Device buffers are the
+ * caller's. GC_ERR_STATE before gc_siren_set. */
+int gc_siren_eval(gc_ctx *ctx, const float *x_dev, int64_t n, float *y_dev, float *J_dev);
+
+/* The physical field the push uses at n points x_dev (scaled positions): field_dev
+ * (n x 24 FP32, device) = B (T, 3), E (V/m, 3), dB[d][c] = dB_c/dR_d (T/m, 9),
+ * dE[d][c] (V/m^2, 9), from the network's outputs and Jacobian by the product rule. */
+int gc_siren_field(gc_ctx *ctx, const float *x_dev, int64_t n, float *field_dev);
+
+/* Training targets: the loaded grid's trilinear interpolant of all eight channels at n
+ * scaled points x_dev, scaled as the network's outputs, into t_dev (n x 8, device). Needs
+ * gc_field_load and gc_siren_set (for the scaling). */
+int gc_field_targets(gc_ctx *ctx, const float *x_dev, int64_t n, float *t_dev);
+
+/* Mean squared error over n samples (n a multiple of 128) and all eight outputs, and its
+ * gradient with respect to the parameters (grad_dev: GC_SIREN_NPARAMS FP32, device, or NULL
+ * to keep it internal), computed by the training's forward and backward passes.
+ * x_dev: n x 3, t_dev: n x 8 (device). loss_out: host, may be NULL. */
+int gc_siren_loss_grad(gc_ctx *ctx, const float *x_dev, const float *t_dev, int64_t n, float *grad_dev,
+                       double *loss_out);
+
+typedef struct {
+    const float *samples;      /* n_samples x 3 scaled positions (x = R / r_max) */
+    int32_t samples_on_device; /* 1: device pointer, 0: host */
+    int32_t pad;
+    int64_t batch;             /* samples per Adam step, a multiple of 128 */
+    double lr, beta1, beta2, eps; /* Adam (Kingma & Ba 2015) */
+} gc_fit_desc;
+
+/* Fit the loaded network to the loaded grid field: targets from gc_field_targets at the
+ * samples, then n_epochs passes over the samples in order, one Adam step per batch (a last
+ * partial batch is dropped). loss_out (host, n_epochs floats, may be NULL) receives each
+ * epoch's mean batch loss measured before the batch's update. */
+int gc_field_fit(gc_ctx *ctx, const gc_fit_desc *f, int64_t n_samples, int n_epochs, float *loss_out);
+
+/* Field source of gc_advance: GC_FIELD_GRID (default) or GC_FIELD_SIREN (needs
+ * gc_siren_set; FP32_MIXED precision only). */
+int gc_field_select(gc_ctx *ctx, int source);
+
 /* Device memory gc_advance_noalloc keeps for its own use on every GPU that loads the
  * library (held until the process exits), and the most ensembles it accepts. */
 #define GC_NOALLOC_SCRATCH_BYTES 40960

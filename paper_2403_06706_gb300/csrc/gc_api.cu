@@ -15,6 +15,7 @@
 
 #include "../../include/gcpush.h"
 #include "gc_internal.h"
+#include "gc_neural.h"
 #include "gc_sort.h"
 
 namespace {
@@ -166,6 +167,10 @@ struct gc_ctx {
     bool in_id_order = true; // slot k holds the k-th smallest id
     bool ids_dense = true;   // ids are a permutation of [id_lo, id_lo + n)
     uint32_t id_lo = 0;
+
+    // neural field (SIREN) and the field source of gc_advance
+    gcn::Neural nn;
+    int field_source = GC_FIELD_GRID;
 
     // launch shape
     int block = 128;
@@ -646,6 +651,7 @@ void gc_destroy(gc_ctx *c)
     if (c->d_clock) cudaFree(c->d_clock);
     if (c->h_clock) cudaFreeHost(c->h_clock);
     gcp::sort_free(c->sortw);
+    gcn::neural_free(c->nn);
     for (cudaEvent_t e : c->ev_pool)
         cudaEventDestroy(e);
     delete c;
@@ -1242,6 +1248,140 @@ int gc_set_clock(gc_ctx *c, double t, int64_t step)
         return fail(GC_ERR_INVALID, "gc_set_clock: bad argument");
     c->t = t;
     c->step = step;
+    return GC_OK;
+}
+
+
+// ----------------------------------------------------------------------------- neural field
+static int nn_ready(gc_ctx *c, const char *who)
+{
+    if (!c) return fail(GC_ERR_INVALID, "%s: null context", who);
+    if (!c->nn.ready) return fail(GC_ERR_STATE, "%s: no network (call gc_siren_set first)", who);
+    return GC_OK;
+}
+
+static gcn::GridRef grid_ref(const gc_ctx *c)
+{
+    gcn::GridRef g;
+    g.nodes = c->d_grid;
+    g.is_f64 = c->gh.is_f64;
+    g.n_r = c->gh.n_r;
+    g.n_th = c->gh.n_th;
+    g.n_ph = c->gh.n_ph;
+    g.r_min = c->gh.r_min;
+    g.dr = c->gh.dr;
+    return g;
+}
+
+int gc_siren_set(gc_ctx *c, const gc_siren_desc *d, const float *params, int params_on_device)
+{
+    if (!c || !d || !params) return fail(GC_ERR_INVALID, "gc_siren_set: null argument");
+    if (!(d->omega0 > 0.0) || !(d->r_max_au > 0.0) || !(d->B_scale > 0.0) || !(d->E_scale > 0.0))
+        return fail(GC_ERR_INVALID, "gc_siren_set: omega0, r_max_au, B_scale and E_scale must be > 0");
+    TRY(set_device(c));
+    drop_graphs(c);
+    cudaError_t e = gcn::neural_set(c->nn, params, params_on_device != 0, d->omega0, d->r_max_au * kAU, d->B_scale,
+                                    d->E_scale, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? GC_ERR_NOMEM : GC_ERR_CUDA, "gc_siren_set: %s",
+                    cudaGetErrorString(e));
+    return GC_OK;
+}
+
+int gc_siren_get(gc_ctx *c, float *params_host)
+{
+    TRY(nn_ready(c, "gc_siren_get"));
+    if (!params_host) return fail(GC_ERR_INVALID, "gc_siren_get: null output");
+    TRY(set_device(c));
+    CUDA_TRY(cudaMemcpyAsync(params_host, c->nn.P, (size_t)GC_SIREN_NPARAMS * sizeof(float), cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GC_OK;
+}
+
+static int nn_check_tc(gc_ctx *c, const char *who)
+{
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int te = gcs::read_error(c->stream);
+    if (!te) te = gcn::neural_read_error(c->nn, c->stream);
+    if (te) return fail(GC_ERR_DEVICE_ANOMALY, "%s: a tensor-core pipeline wait ran out (code %d)", who, te);
+    return GC_OK;
+}
+
+int gc_siren_eval(gc_ctx *c, const float *x_dev, int64_t n, float *y_dev, float *J_dev)
+{
+    TRY(nn_ready(c, "gc_siren_eval"));
+    if (n < 0 || (n > 0 && (!x_dev || !y_dev))) return fail(GC_ERR_INVALID, "gc_siren_eval: bad arguments");
+    TRY(set_device(c));
+    CUDA_TRY(gcn::neural_eval(c->nn, x_dev, n, y_dev, J_dev, c->stream));
+    return nn_check_tc(c, "gc_siren_eval");
+}
+
+int gc_siren_field(gc_ctx *c, const float *x_dev, int64_t n, float *field_dev)
+{
+    TRY(nn_ready(c, "gc_siren_field"));
+    if (n < 0 || (n > 0 && (!x_dev || !field_dev))) return fail(GC_ERR_INVALID, "gc_siren_field: bad arguments");
+    TRY(set_device(c));
+    CUDA_TRY(gcn::neural_field(c->nn, x_dev, n, field_dev, c->stream));
+    return nn_check_tc(c, "gc_siren_field");
+}
+
+int gc_field_targets(gc_ctx *c, const float *x_dev, int64_t n, float *t_dev)
+{
+    TRY(nn_ready(c, "gc_field_targets"));
+    if (!c->has_field) return fail(GC_ERR_STATE, "gc_field_targets: no field loaded");
+    if (n < 0 || (n > 0 && (!x_dev || !t_dev))) return fail(GC_ERR_INVALID, "gc_field_targets: bad arguments");
+    TRY(set_device(c));
+    CUDA_TRY(gcn::neural_targets(c->nn, grid_ref(c), x_dev, n, t_dev, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GC_OK;
+}
+
+int gc_siren_loss_grad(gc_ctx *c, const float *x_dev, const float *t_dev, int64_t n, float *grad_dev,
+                       double *loss_out)
+{
+    TRY(nn_ready(c, "gc_siren_loss_grad"));
+    if (!x_dev || !t_dev || n <= 0 || n % 128 != 0 || n > ((int64_t)1 << 30))
+        return fail(GC_ERR_INVALID, "gc_siren_loss_grad: need device x and t and n a positive multiple of 128");
+    TRY(set_device(c));
+    double loss = 0.0;
+    CUDA_TRY(gcn::neural_loss_grad(c->nn, x_dev, t_dev, n, grad_dev, &loss, c->stream));
+    TRY(nn_check_tc(c, "gc_siren_loss_grad"));
+    if (loss_out) *loss_out = loss;
+    return GC_OK;
+}
+
+int gc_field_fit(gc_ctx *c, const gc_fit_desc *f, int64_t n_samples, int n_epochs, float *loss_out)
+{
+    TRY(nn_ready(c, "gc_field_fit"));
+    if (!c->has_field) return fail(GC_ERR_STATE, "gc_field_fit: no field loaded");
+    if (!f || !f->samples || n_epochs < 0 || f->batch <= 0 || f->batch % 128 != 0 || f->batch > ((int64_t)1 << 24) ||
+        n_samples < f->batch)
+        return fail(GC_ERR_INVALID, "gc_field_fit: need samples, batch a positive multiple of 128 (<= 2^24) "
+                                    "and n_samples >= batch");
+    if (!(f->lr > 0.0) || !(f->beta1 >= 0.0 && f->beta1 < 1.0) || !(f->beta2 >= 0.0 && f->beta2 < 1.0) ||
+        !(f->eps > 0.0))
+        return fail(GC_ERR_INVALID, "gc_field_fit: need lr > 0, 0 <= beta1, beta2 < 1, eps > 0");
+    TRY(set_device(c));
+    drop_graphs(c);
+    CUDA_TRY(gcn::neural_fit(c->nn, grid_ref(c), f->samples, f->samples_on_device != 0, n_samples, f->batch,
+                             n_epochs, f->lr, f->beta1, f->beta2, f->eps, loss_out, c->stream));
+    return nn_check_tc(c, "gc_field_fit");
+}
+
+int gc_field_select(gc_ctx *c, int source)
+{
+    if (!c) return fail(GC_ERR_INVALID, "gc_field_select: null context");
+    if (source != GC_FIELD_GRID && source != GC_FIELD_SIREN)
+        return fail(GC_ERR_INVALID, "gc_field_select: unknown source %d", source);
+    if (source == GC_FIELD_SIREN) {
+        TRY(nn_ready(c, "gc_field_select"));
+        if (c->opt.precision != GC_PREC_FP32_MIXED)
+            return fail(GC_ERR_UNSUPPORTED, "gc_field_select: the neural field runs with GC_PREC_FP32_MIXED only");
+    }
+    drop_graphs(c);
+    c->field_source = source;
     return GC_OK;
 }
 

@@ -1,0 +1,425 @@
+// gc_siren_eval.cu -- fused evaluation of the SIREN neural field and its Jacobian on the
+// tensor cores (tcgen05, TMA, tensor memory).
+//
+// Forward-mode differentiation carries three tangent rows beside every value row: for a
+// point x the rows are h_k and t_{k,j} = dh_k/dx_j (j = 0..2), with
+//   layer 1:  z = w0 (W1 x + b1),   h1 = sin z,   t1_j = w0 cos(z) W1[:, j]
+//   layer k:  z = W_k h_{k-1} + b_k, h_k = sin z, t_{k,j} = cos(z) * (W_k t_{k-1,j})
+//   output:   y = W5 h4 + b5,       J[:, j] = W5 t_{4,j}.
+// A tile is 64 points = 256 rows (row 4p + q: q = 0 value, q = 1..3 tangents). Hidden
+// layers run as D = W_k . H^T on the tensor cores (M = 128 output features per half,
+// N = 256 rows, K = 256), so that each accumulator lane holds one feature and the four rows
+// of a point sit in adjacent columns: the epilogue thread of a feature computes sin and cos
+// of the value row once and scales its own three tangent columns, with no data exchange.
+// Activations go back to shared memory in the MN-major 128-byte-swizzled layout that the
+// next layer reads as its B operand. The output layer runs as rows x W5^T (M = 128 rows,
+// N = 16 with W5 zero-padded). Weights stream through a 3-stage TMA ring (32 KB chunks of
+// 64 input features x 256 outputs); the first layer runs on the CUDA cores.
+//
+// Warp roles (320 threads): warps 0-7 compute (feature f = 128 (w / 4) + 32 (w % 4) + lane;
+// warp w may only touch tensor-memory lanes 32 (w % 4) .. + 31), warp 8 lane 0 issues the
+// MMAs (warp 8 also owns the tensor-memory allocation), warp 9 lane 0 issues the TMA loads.
+// Every wait is bounded: a wait that runs out sets the kernel's error word and an abort flag
+// that makes all roles leave their loops; the CTA then waits for its own copies and MMAs
+// and frees its tensor memory.
+#include <cstdio>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "gc_siren.h"
+#include "gc_tc.cuh"
+
+namespace gcs {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kPts = 64;                        // points per tile
+constexpr int kStagesW = 3;                     // weight ring depth
+constexpr uint32_t kChunkBytes = 256u * 128u;   // 256 rows x 64 bf16
+constexpr uint32_t kW5Bytes = 4u * 16u * 128u;  // W5 padded: 4 boxes of 16 rows x 64 bf16
+constexpr uint32_t kHBytes = 32u * 4u * 1024u;  // 32 K-groups x 4 MN-blocks of 1024 B
+constexpr int kChunksPerTile = 3 * 4 + 1;
+constexpr int kComputeThreads = 256;
+constexpr int kThreads = 320;
+constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + 1024 + 128;
+
+struct EvalParams {
+    const float *P;  // master parameters
+    const float *x;  // n x 3
+    int64_t n;
+    SirenOut out;
+    float omega0;
+    int *err;        // error word (device), set when a wait runs out
+};
+
+// sin and cos after a Cody-Waite reduction by 2 pi (2 pi split into a float and its
+// remainder), so that the hardware approximations see |r| <= pi
+__device__ __forceinline__ void sincos_rr(float z, float &s, float &c)
+{
+    const float k = rintf(z * 0.159154943091895336f);
+    float r = fmaf(-k, 6.28318548202514648f, z);
+    r = fmaf(-k, -1.74845553e-7f, r);
+    s = __sinf(r);
+    c = __cosf(r);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// 8 consecutive rows (mn0 .. mn0 + 7, mn0 % 8 == 0) of one feature into the MN-major
+// activation buffer; hrow points at the feature's 128-byte row of its K-group's first atom
+__device__ __forceinline__ void store_rows8(uint8_t *hrow, uint32_t rsw, uint32_t mn0, const float (&o)[8])
+{
+    uint4 pk;
+    pk.x = pack_bf16(o[0], o[1]);
+    pk.y = pack_bf16(o[2], o[3]);
+    pk.z = pack_bf16(o[4], o[5]);
+    pk.w = pack_bf16(o[6], o[7]);
+    const uint32_t ch = ((mn0 & 63u) >> 3) ^ rsw;
+    *reinterpret_cast<uint4 *>(hrow + (mn0 >> 6) * 1024u + ch * 16u) = pk;
+}
+
+// bounded wait that also gives up when another role of the CTA has aborted
+__device__ __forceinline__ bool wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort, int *err, int code)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > kWaitNs) break;
+    }
+    *abort = 1;
+    atomicExch(err, code);
+    return false;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    siren_eval_kernel(const __grid_constant__ CUtensorMap mwh, const __grid_constant__ CUtensorMap mw5,
+                      const EvalParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sH = smem;
+    uint8_t *sW = smem + kHBytes;
+    uint64_t *full = (uint64_t *)(sW + kStagesW * kChunkBytes);
+    uint64_t *empty = full + kStagesW;
+    uint64_t *h_ready = empty + kStagesW;
+    uint64_t *acc_ready = h_ready + 1;
+    uint64_t *fin = acc_ready + 1;
+    uint32_t *tmem_slot = (uint32_t *)(fin + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_tiles = (p.n + kPts - 1) / kPts;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesW; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(h_ready, kComputeThreads);
+        mbar_init(acc_ready, 1);
+        mbar_init(fin, 1);
+        *abort = 0;
+        mbar_fence_init();
+    }
+    if (warp == 8) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 9) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int c = 0; c < kChunksPerTile; ++c) {
+                    const uint32_t s = g % kStagesW;
+                    if (!wait_abort(&empty[s], ((g / kStagesW) & 1u) ^ 1u, abort, p.err, 11)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *dst = sW + s * kChunkBytes;
+                    if (c < 12) {
+                        mbar_expect_tx(&full[s], kChunkBytes);
+                        tma_load_2d(dst, &mwh, (c & 3) * 64, (c >> 2) * 256, &full[s]);
+                    } else {
+                        mbar_expect_tx(&full[s], kW5Bytes);
+                        for (int kb = 0; kb < 4; ++kb)
+                            tma_load_2d(dst + kb * 2048, &mw5, kb * 64, 0, &full[s]);
+                    }
+                    ++g;
+                }
+            }
+            // the copies still in flight land before the CTA's shared memory is released
+            for (uint32_t j = g > (uint32_t)kStagesW ? g - kStagesW : 0u; j < g; ++j)
+                mbar_wait(&full[j % kStagesW], (j / kStagesW) & 1u);
+        }
+    } else if (warp == 8) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t id_hid = idesc_bf16_f32(128, 256, 0, 1);
+            const uint32_t id_out = idesc_bf16_f32(128, 16, 1, 0);
+            const uint32_t hb = smem_u32(sH);
+            uint32_t g = 0, nh = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int L = 0; L < 3 && ok; ++L) {
+                    if (!wait_abort(h_ready, nh & 1u, abort, p.err, 12)) {
+                        ok = false;
+                        break;
+                    }
+                    ++nh;
+                    tc_fence_after();
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const uint32_t s = g % kStagesW;
+                        if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 13)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t wb = smem_u32(sW + s * kChunkBytes);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks)
+                                mma_bf16(tmem + h * 256, desc_sw128(wb + h * 16384 + ks * 32),
+                                         desc_sw128_mn(hb + (kb * 4 + ks) * 8192, 1024, 4096), id_hid,
+                                         (kb | ks) ? 1u : 0u);
+                        mma_commit(&empty[s]);
+                        ++g;
+                    }
+                    if (ok) mma_commit(acc_ready);
+                }
+                if (!ok) break;
+                // output layer: rows x W5^T, two M-tiles of 128 rows into columns 0-15, 16-31
+                if (!wait_abort(h_ready, nh & 1u, abort, p.err, 14)) break;
+                ++nh;
+                tc_fence_after();
+                const uint32_t s = g % kStagesW;
+                if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 15)) break;
+                tc_fence_after();
+                const uint32_t wb = smem_u32(sW + s * kChunkBytes);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int k16 = 0; k16 < 16; ++k16)
+                        mma_bf16(tmem + mt * 16, desc_sw128_mn(hb + mt * 2048 + k16 * 8192, 1024, 4096),
+                                 desc_sw128(wb + (k16 >> 2) * 2048 + (k16 & 3) * 32), id_out, k16 ? 1u : 0u);
+                mma_commit(&empty[s]);
+                ++g;
+                mma_commit(acc_ready);
+            }
+            // all MMAs of this CTA complete before its tensor memory is released
+            mma_commit(fin);
+            mbar_wait(fin, 0);
+        }
+    } else {
+        // ------------------------------------------------------------ compute warps
+        const int lq = warp & 3, hh = warp >> 2;
+        const int f = hh * 128 + lq * 32 + lane;
+        const float w0 = p.omega0;
+        const float w1x = p.P[siren_oW(1) + 3 * f], w1y = p.P[siren_oW(1) + 3 * f + 1],
+                    w1z = p.P[siren_oW(1) + 3 * f + 2], b1 = p.P[siren_oB(1) + f];
+        float bl[3];
+#pragma unroll
+        for (int L = 0; L < 3; ++L)
+            bl[L] = p.P[siren_oB(L + 2) + f];
+        float b5[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            b5[o] = p.P[siren_oB(5) + o];
+        const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16);
+        uint8_t *hrow = sH + (f >> 3) * 4096 + (f & 7) * 128;
+        const uint32_t rsw = (uint32_t)(f & 7);
+        uint32_t na = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const int64_t base = t * kPts;
+            // layer 1 on the CUDA cores
+#pragma unroll 1
+            for (int p2 = 0; p2 < kPts / 2; ++p2) {
+                float o[8];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int64_t P = base + 2 * p2 + e;
+                    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+                    if (P < p.n) {
+                        x0 = __ldg(p.x + 3 * P);
+                        x1 = __ldg(p.x + 3 * P + 1);
+                        x2 = __ldg(p.x + 3 * P + 2);
+                    }
+                    const float z = w0 * fmaf(w1x, x0, fmaf(w1y, x1, fmaf(w1z, x2, b1)));
+                    float sn, cs;
+                    sincos_rr(z, sn, cs);
+                    const float wc = w0 * cs;
+                    o[4 * e] = sn;
+                    o[4 * e + 1] = wc * w1x;
+                    o[4 * e + 2] = wc * w1y;
+                    o[4 * e + 3] = wc * w1z;
+                }
+                store_rows8(hrow, rsw, 8u * p2, o);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(h_ready);
+            // hidden layers 2-4: epilogue of D = W_k H^T
+            for (int L = 0; L < 3; ++L) {
+                if (!wait_abort(acc_ready, na & 1u, abort, p.err, 16)) {
+                    ok = false;
+                    break;
+                }
+                ++na;
+                tc_fence_after();
+                const float b = bl[L];
+#pragma unroll 1
+                for (int c = 0; c < 8; ++c) {
+                    float v[32];
+                    tmem_ld32(lane_base + hh * 256 + c * 32, v);
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp) {
+                        float o[8];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int q0 = 8 * pp + 4 * e;
+                            float sn, cs;
+                            sincos_rr(v[q0] + b, sn, cs);
+                            o[4 * e] = sn;
+                            o[4 * e + 1] = cs * v[q0 + 1];
+                            o[4 * e + 2] = cs * v[q0 + 2];
+                            o[4 * e + 3] = cs * v[q0 + 3];
+                        }
+                        store_rows8(hrow, rsw, (uint32_t)(c * 32 + 8 * pp), o);
+                    }
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                mbar_arrive(h_ready);
+            }
+            if (!ok) break;
+            // output layer
+            if (!wait_abort(acc_ready, na & 1u, abort, p.err, 17)) break;
+            ++na;
+            tc_fence_after();
+            float v[16];
+            tmem_ld16(lane_base + hh * 16, v);
+            tc_fence_before();
+            const int pr = hh * 128 + lq * 32 + lane;
+            const int q = pr & 3;
+            const int64_t P = base + (pr >> 2);
+            if (p.out.field == nullptr) {
+                if (P < p.n) {
+                    if (q == 0) {
+#pragma unroll
+                        for (int o = 0; o < 8; ++o)
+                            p.out.y[P * 8 + o] = v[o] + b5[o];
+                    } else if (p.out.J) {
+#pragma unroll
+                        for (int o = 0; o < 8; ++o)
+                            p.out.J[(P * 8 + o) * 3 + (q - 1)] = v[o];
+                    }
+                }
+            } else {
+                // physical field: B = B_s y_B (AU/r)^2, E = E_s y_E (AU/r) at R = r_max x;
+                // gradients by the product rule with d/dR = (1/r_max) d/dx
+                const unsigned full_mask = 0xffffffffu;
+                const int src = lane & ~3;
+                float yv[6];
+#pragma unroll
+                for (int o = 0; o < 6; ++o)
+                    yv[o] = __shfl_sync(full_mask, v[o] + b5[o], src);
+                if (P < p.n) {
+                    const double au = 1.495978707e11;
+                    const float rm = (float)p.out.r_max;
+                    const float X0 = __ldg(p.x + 3 * P) * rm, X1 = __ldg(p.x + 3 * P + 1) * rm,
+                                X2 = __ldg(p.x + 3 * P + 2) * rm;
+                    const float r2 = X0 * X0 + X1 * X1 + X2 * X2;
+                    const float ir = rsqrtf(r2);
+                    const float a = (float)au * ir;                   // AU / r
+                    const float bs = (float)p.out.B_scale * a * a;    // B per unit y_B
+                    const float es = (float)p.out.E_scale * a;        // E per unit y_E
+                    float *dst = p.out.field + P * 24;
+                    if (q == 0) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            dst[c] = bs * yv[c];
+                            dst[3 + c] = es * yv[3 + c];
+                        }
+                    } else {
+                        const int d = q - 1;
+                        const float Xd = d == 0 ? X0 : (d == 1 ? X1 : X2);
+                        const float irm = 1.0f / rm;
+                        const float ur = Xd * ir * ir;  // R_d / r^2
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            dst[6 + 3 * d + c] = bs * (v[c] * irm - 2.0f * yv[c] * ur);
+                            dst[15 + 3 * d + c] = es * (v[3 + c] * irm - yv[3 + c] * ur);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+} // namespace
+
+cudaError_t siren_maps(SirenNet &net)
+{
+    cudaError_t e = make_map_bf16(&net.map_wh, net.Wh, 256, 3 * 256, 256);
+    if (e == cudaSuccess) e = make_map_bf16(&net.map_w5, net.W5p, 256, 16, 16);
+    return e;
+}
+
+int siren_eval_grid(int64_t n)
+{
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    const int64_t tiles = (n + kPts - 1) / kPts;
+    return (int)(tiles < n_sm ? tiles : n_sm);
+}
+
+cudaError_t siren_eval(const SirenNet &net, const float *x, int64_t n, const SirenOut &out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (!net.err) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(siren_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    EvalParams p;
+    p.P = net.P;
+    p.x = x;
+    p.n = n;
+    p.out = out;
+    p.omega0 = net.omega0;
+    p.err = net.err;
+    siren_eval_kernel<<<siren_eval_grid(n), kThreads, kSmemBytes, s>>>(net.map_wh, net.map_w5, p);
+    return cudaGetLastError();
+}
+
+} // namespace gcs

@@ -14,8 +14,18 @@
 
 namespace tc {
 
-// bounded spin of mbarrier waits: about a second, then the caller reports an error
-constexpr uint32_t kWaitLimit = 1u << 22;
+// Waits on mbarriers are bounded in time: a wait gives up after kWaitNs of the global
+// timer (each poll may suspend the thread for at most kPollNs), and its caller reports an
+// error instead of hanging.
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint32_t kPollNs = 20000u;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -44,35 +54,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One poll: has the phase with the given parity completed?
+// One poll: has the phase with the given parity completed? (may suspend up to kPollNs)
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 {
     uint32_t done;
     asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(done)
-                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "r"(smem_u32(bar)), "r"(parity), "r"(kPollNs)
                  : "memory");
     return done != 0;
 }
 
-// Wait for the phase with the given parity to complete; false after kWaitLimit polls.
+// Wait for the phase with the given parity to complete; false after kWaitNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
-    const uint32_t a = smem_u32(bar);
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (done)
-            return true;
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
     }
-    return false;
 }
 
 // ---------------------------------------------------------------------------- TMA

@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libgcpush.so")
-SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu", "gc_noalloc.cu", "gc_siren.cu")
+SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu", "gc_noalloc.cu", "gc_siren.cu", "gc_siren_eval.cu",
+           "gc_neural.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
@@ -127,6 +128,21 @@ class StatsOut(C.Structure):
                 ("push_ms", C.c_double), ("sorts", C.c_uint64), ("sort_ms", C.c_double)]
 
 
+class SirenDesc(C.Structure):
+    _fields_ = [("omega0", C.c_double), ("r_max_au", C.c_double), ("B_scale", C.c_double),
+                ("E_scale", C.c_double)]
+
+
+class FitDesc(C.Structure):
+    _fields_ = [("samples", C.c_void_p), ("samples_on_device", C.c_int32), ("pad", C.c_int32),
+                ("batch", C.c_int64), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double)]
+
+
+SIREN_NPARAMS = 200456
+FIELD_GRID, FIELD_SIREN = 0, 1
+
+
 class LaunchChoice(C.Structure):
     _fields_ = [("block", C.c_int32), ("grid_waves", C.c_int32), ("steps_per_launch", C.c_int32),
                 ("sort_every", C.c_int32), ("particle_steps_per_s", C.c_double),
@@ -136,7 +152,9 @@ class LaunchChoice(C.Structure):
 EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_particles_inject",
            "gc_advance", "gc_tally", "gc_particles_get", "gc_particles_set", "gc_stats",
            "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc",
-           "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn", "gc_gemm_bf16")
+           "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn", "gc_gemm_bf16", "gc_siren_set", "gc_siren_get",
+           "gc_siren_eval", "gc_siren_field", "gc_field_targets", "gc_siren_loss_grad", "gc_field_fit",
+           "gc_field_select")
 
 _lib = None
 
@@ -169,6 +187,14 @@ def load(path: str | None = None):
         "gc_gemm_bf16": (C.c_int, [vp, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    vp]),
         "gc_autotune": (C.c_int, [vp, C.c_double, C.c_int64, C.POINTER(LaunchChoice)]),
+        "gc_siren_set": (C.c_int, [vp, C.POINTER(SirenDesc), vp, C.c_int]),
+        "gc_siren_get": (C.c_int, [vp, vp]),
+        "gc_siren_eval": (C.c_int, [vp, vp, C.c_int64, vp, vp]),
+        "gc_siren_field": (C.c_int, [vp, vp, C.c_int64, vp]),
+        "gc_field_targets": (C.c_int, [vp, vp, C.c_int64, vp]),
+        "gc_siren_loss_grad": (C.c_int, [vp, vp, vp, C.c_int64, vp, C.POINTER(C.c_double)]),
+        "gc_field_fit": (C.c_int, [vp, C.POINTER(FitDesc), C.c_int64, C.c_int, vp]),
+        "gc_field_select": (C.c_int, [vp, C.c_int]),
         "gc_sort": (C.c_int, [vp]),
         "gc_version": (C.c_int, []),
         "gc_set_clock": (C.c_int, [vp, C.c_double, C.c_int64]),
@@ -340,6 +366,60 @@ class Context:
         _check(load().gc_particles_set(self._h, C.byref(s)), "gc_particles_set")
 
     # tallies -----------------------------------------------------------------
+    # neural field --------------------------------------------------------------
+    def siren_set(self, params, omega0: float = 30.0, r_max_au: float = 2.5, B_scale: float = 1.0,
+                  E_scale: float = 1.0):
+        """Load SIREN parameters (numpy float32 array or torch CUDA tensor of SIREN_NPARAMS)."""
+        d = SirenDesc(omega0, r_max_au, B_scale, E_scale)
+        if hasattr(params, "data_ptr"):
+            assert params.numel() == SIREN_NPARAMS and params.is_contiguous()
+            _check(load().gc_siren_set(self._h, C.byref(d), params.data_ptr(), 1), "gc_siren_set")
+        else:
+            a = np.ascontiguousarray(params, dtype=np.float32)
+            assert a.size == SIREN_NPARAMS
+            _check(load().gc_siren_set(self._h, C.byref(d), a.ctypes.data, 0), "gc_siren_set")
+
+    def siren_get(self) -> np.ndarray:
+        a = np.empty(SIREN_NPARAMS, dtype=np.float32)
+        _check(load().gc_siren_get(self._h, a.ctypes.data), "gc_siren_get")
+        return a
+
+    def siren_eval(self, x, y, J=None):
+        """Raw outputs at x (torch CUDA float32 n x 3) into y (n x 8) and J (n x 8 x 3)."""
+        _check(load().gc_siren_eval(self._h, x.data_ptr(), x.shape[0], y.data_ptr(),
+                                    None if J is None else J.data_ptr()), "gc_siren_eval")
+
+    def siren_field(self, x, field):
+        _check(load().gc_siren_field(self._h, x.data_ptr(), x.shape[0], field.data_ptr()), "gc_siren_field")
+
+    def field_targets(self, x, t):
+        _check(load().gc_field_targets(self._h, x.data_ptr(), x.shape[0], t.data_ptr()), "gc_field_targets")
+
+    def siren_loss_grad(self, x, t, grad=None) -> float:
+        loss = C.c_double()
+        _check(load().gc_siren_loss_grad(self._h, x.data_ptr(), t.data_ptr(), x.shape[0],
+                                         None if grad is None else grad.data_ptr(), C.byref(loss)),
+               "gc_siren_loss_grad")
+        return loss.value
+
+    def field_fit(self, samples, n_epochs: int, batch: int = 65536, lr: float = 1e-4, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-8) -> np.ndarray:
+        """Fit the network to the loaded grid at samples (n x 3 scaled positions; numpy or
+        torch CUDA); returns the per-epoch mean loss."""
+        on_dev = hasattr(samples, "data_ptr")
+        if on_dev:
+            ptr, n = samples.data_ptr(), samples.shape[0]
+        else:
+            samples = np.ascontiguousarray(samples, dtype=np.float32)
+            ptr, n = samples.ctypes.data, samples.shape[0]
+        f = FitDesc(ptr, int(on_dev), 0, batch, lr, beta1, beta2, eps)
+        out = np.zeros(max(n_epochs, 1), dtype=np.float32)
+        _check(load().gc_field_fit(self._h, C.byref(f), n, n_epochs, out.ctypes.data), "gc_field_fit")
+        return out[:n_epochs]
+
+    def field_select(self, source: int):
+        _check(load().gc_field_select(self._h, source), "gc_field_select")
+
     def tally_arm(self, cadence=100, n_mu=32, n_E=32, n_r=64, n_age=32, t_start_s=0.0,
                   E_lo_keV=5.0, E_hi_keV=600.0, r_lo_au=0.1, r_hi_au=2.5, age_max_s=86400.0,
                   rwin_lo_au=0.9, rwin_hi_au=1.1, age_young_s=1200.0):
