@@ -50,6 +50,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PUSH_TRAFFIC_BYTES = 492_170_000 + 373_810_000
 PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+# Neural field: tensor-core work of one evaluation with its Jacobian (value + 3 tangent
+# rows through three 256 x 256 layers and the 256 x 8 output layer, FMA = 2 flop)
+NEURAL_FLOP_PER_EVAL = 3 * 4 * 256 * 256 * 2 + 4 * 256 * 8 * 2
+NEURAL_STEPS_PER_CALL = 10
 
 
 def workload(n_per_lambda: int = 1_000_000):
@@ -206,6 +210,90 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def neural_bench(args, nodes, local, stream, rank):
+    """The neural-field path: train the SIREN on samples of the grid interpolant, measure its
+    field error against the grid, then time the split-step push with the network as the
+    field source (10^7 electrons)."""
+    import torch
+
+    from paper_2403_06706_gb300 import gcpush, shard
+
+    wn = synth.c4_neural(args.neural_particles)
+    X = wn.extra
+    epochs = X["epochs"] if args.neural_epochs is None else args.neural_epochs
+    w = wn.wind
+    c = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wn.seed, dt_init=wn.dt,
+                       id_base=shard.id_base(rank, wn.n_particles))
+    c.field_load(nodes, w.r_min_au, w.r_max_au)
+    c.siren_set(synth.siren_init(seed=0), omega0=X["omega0"], r_max_au=w.r_max_au, B_scale=w.B1,
+                E_scale=w.B1 * w.u_sw)
+    xs = torch.from_numpy(synth.siren_samples(X["n_samples"], w)).to("cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = c.field_fit(xs, n_epochs=epochs, batch=X["batch"], lr=X["lr"])
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    del xs
+    # field error against the grid interpolant on held-out points (scaled channels)
+    xv = torch.from_numpy(synth.siren_samples(1 << 20, w, seed=1)).to("cuda")
+    y = torch.empty((xv.shape[0], 8), device="cuda")
+    t = torch.empty((xv.shape[0], 8), device="cuda")
+    c.siren_eval(xv, y)
+    c.field_targets(xv, t)
+    torch.cuda.synchronize()
+    d = (y - t).double()
+    err = {g: float(torch.sqrt((d[:, sl] ** 2).mean() / (t[:, sl].double() ** 2).mean()))
+           for g, sl in (("B", slice(0, 3)), ("E", slice(3, 6)), ("absB", slice(6, 7)))}
+    del xv, y, t, d
+    # push with the network as the field source
+    c.field_select(gcpush.FIELD_SIREN)
+    c.inject(list(wn.ensembles))
+    for _ in range(args.warmup):
+        c.advance(wn.dt, NEURAL_STEPS_PER_CALL)
+    torch.cuda.synchronize()
+    s0 = c.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        c.advance(wn.dt, NEURAL_STEPS_PER_CALL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s1 = c.stats()
+    n = wn.n_particles
+    evals = s1["field_evals"] - s0["field_evals"]
+    fms = s1["field_ms"] - s0["field_ms"]
+    achieved = NEURAL_FLOP_PER_EVAL * evals / (fms / 1e3) / 1e12
+    peaks = _measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained")
+    c.close()
+    return {
+        "workload": wn.name, "particles": n, "value": n * NEURAL_STEPS_PER_CALL * args.steps / (ms / 1e3),
+        "unit": UNIT, "ms_per_step": ms / (args.steps * NEURAL_STEPS_PER_CALL),
+        "roofline": {"bound": "tensor", "kernel": "siren_eval_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                     "peak_basis": "measured bf16 cuBLAS, sustained (MEASURED_PEAKS.json)",
+                     "flop_per_eval": NEURAL_FLOP_PER_EVAL, "evals": evals,
+                     "eval_share_of_step": fms / ms},
+        "training": {"samples": X["n_samples"], "epochs": epochs, "batch": X["batch"], "lr": X["lr"],
+                     "seconds": t_fit, "samples_per_s": X["n_samples"] * epochs / t_fit,
+                     "loss_first_epoch": float(loss[0]) if len(loss) else None,
+                     "loss_last_epoch": float(loss[-1]) if len(loss) else None},
+        "field_rel_rms_vs_grid": err,
+        "footprint_bytes": {"network_bf16": 2 * (3 * 65536 + 2048) + 4 * (768 + 4 * 256 + 8),
+                            "grid_f32": int(nodes.nbytes)},
+    }
+
+
+def _measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +304,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-neural", action="store_true")
+    ap.add_argument("--neural-particles", type=int, default=10_000_000)
+    ap.add_argument("--neural-epochs", type=int, default=None)
     ap.add_argument("--particles", type=int, default=3_000_000,
                     help="particles per GPU (split over the three lambda ensembles); smaller "
                          "values are for profiler captures")
@@ -374,6 +465,10 @@ def main():
                    "push_steps_per_call": nb_steps, "graph": True, "autotune": choice}
         cb.close()
 
+    neural = None
+    if not args.no_neural:
+        neural = neural_bench(args, nodes, local, stream, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, nodes)
@@ -387,7 +482,7 @@ def main():
             "config": config_dict(wl, n_rank),
             "parallelism": f"particles sharded by id, {world} GPU(s), no data-path collective",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clocks, "fp64_plain": fp64, "batched": batched,
+            "clocks": clocks, "fp64_plain": fp64, "batched": batched, "neural": neural,
             "accuracy": "FP32 path within 1e-4 of the FP64 oracle over the first 1e3 steps; "
                         "FP64 path within 1e-9 (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)",
         }

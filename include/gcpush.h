@@ -154,6 +154,8 @@ typedef struct {
     double push_ms;           /* summed device time of those launches (CUDA events) */
     uint64_t sorts;           /* cell sorts performed */
     double sort_ms;           /* summed device time of the sorts */
+    uint64_t field_evals;     /* field samples of the split-step push (points) */
+    double field_ms;          /* summed device time of those sample launches */
 } gc_stats_out;
 
 /* Create a context on opt->device. *out receives the handle. */
@@ -255,7 +257,10 @@ int gc_gemm_bf16(const void *A, int a_mn, const void *B, int b_mn, float *C, int
  * tensor cores; W1 and the biases stay FP32. The field's derivatives come from the
  * network's exact Jacobian (three forward-mode tangents). */
 #define GC_SIREN_NPARAMS 200456
-enum { GC_FIELD_GRID = 0, GC_FIELD_SIREN = 1 };
+/* field sources of gc_advance: the grid gathered inside the fused push (default), the
+ * neural field, or the grid evaluated through the split-step push's sample buffers (the
+ * neural path's machinery with the grid field: it reproduces GC_FIELD_GRID) */
+enum { GC_FIELD_GRID = 0, GC_FIELD_SIREN = 1, GC_FIELD_GRID_SAMPLED = 2 };
 
 typedef struct {
     double omega0;   /* frequency of the first layer's sine (30 in Sitzmann et al.) */
@@ -307,8 +312,13 @@ typedef struct {
  * epoch's mean batch loss measured before the batch's update. */
 int gc_field_fit(gc_ctx *ctx, const gc_fit_desc *f, int64_t n_samples, int n_epochs, float *loss_out);
 
-/* Field source of gc_advance: GC_FIELD_GRID (default) or GC_FIELD_SIREN (needs
- * gc_siren_set; FP32_MIXED precision only). */
+/* Field source of gc_advance and of later injections: GC_FIELD_GRID (default), or one of
+ * the split-step sources (FP32_MIXED precision only): GC_FIELD_SIREN (needs gc_siren_set)
+ * or GC_FIELD_GRID_SAMPLED. The split-step push advances all particles one evaluation phase
+ * per launch (predictor, corrector, post-step tests, then the start-up of the restarted
+ * particles, Sect. 2.2) with the field sampled in between; it has no cell sort and no graph
+ * replay. Injections under a split-step source take mu_B and the start-up history from that
+ * source. */
 int gc_field_select(gc_ctx *ctx, int source);
 
 /* Device memory gc_advance_noalloc keeps for its own use on every GPU that loads the

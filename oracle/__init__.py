@@ -69,6 +69,9 @@ class Field(C.Structure):
         ("parker_B0", C.c_double), ("parker_rref", C.c_double),
         ("parker_omega", C.c_double), ("parker_u", C.c_double),
         ("dipole_m", C.c_double * 3),
+        ("siren", C.c_void_p), ("siren_omega0", C.c_double), ("siren_rscale", C.c_double),
+        ("siren_Bs", C.c_double), ("siren_Es", C.c_double), ("siren_bf16", C.c_int32),
+        ("pad1", C.c_int32),
     ]
 
 
@@ -202,6 +205,28 @@ def analytic_field(B_unif=(0, 0, 0), E_unif=(0, 0, 0), parker_B0=0.0, parker_rre
     f.parker_omega, f.parker_u = parker_omega, parker_u
     f.parker_E = 1 if parker_E else 0
     f.dipole_m[:] = list(dipole_m)
+    return f
+
+
+def siren_field(params_flat, omega0: float, r_scale: float, B_scale: float, E_scale: float,
+                bf16: bool = False, ideal: bool = True) -> Field:
+    """Neural field (SIREN, oracle/siren.py layout): x = R / r_scale, B = B_scale y_B (AU/r)^2,
+    E = E_scale y_E (AU/r). With bf16 the weights W2..W5 are rounded to bfloat16 here and the
+    values carried between layers inside the evaluation (the tensor-core arithmetic)."""
+    from . import siren as _siren
+    P = np.ascontiguousarray(params_flat, dtype=np.float64).copy()
+    if bf16:
+        for k in range(2, 6):
+            o = _siren.offset(f"W{k}")
+            n = 65536 if k < 5 else 2048
+            P[o:o + n] = _siren.round_bf16(P[o:o + n])
+    f = Field()
+    f.kind = 2
+    f.ideal = 1 if ideal else 0
+    f.siren = P.ctypes.data
+    f.siren_omega0, f.siren_rscale, f.siren_Bs, f.siren_Es = omega0, r_scale, B_scale, E_scale
+    f.siren_bf16 = 1 if bf16 else 0
+    f._keep = P
     return f
 
 

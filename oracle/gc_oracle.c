@@ -12,8 +12,10 @@
  *
  * What it computes, by section of the paper:
  *   - field evaluation: trilinear interpolation of a spherical (r, theta, phi)
- *     grid of node values (Sect. 2.2, the sentence after Eq. 3), or an
- *     analytic field (uniform + Parker spiral + dipole) used by the pins;
+ *     grid of node values (Sect. 2.2, the sentence after Eq. 3), an
+ *     analytic field (uniform + Parker spiral + dipole) used by the pins, or
+ *     a neural field (a SIREN, Sitzmann et al. 2020, evaluated in FP64 with
+ *     its exact Jacobian by forward-mode tangents);
  *   - the relativistic GC right-hand side F(X), X = {R, gamma v_par}: Eqs. 1-3;
  *   - the third-order predictor-corrector: Eqs. 5-6, with the backward-Euler
  *     start-up after injection and after every collision (Sect. 2.2);
@@ -60,7 +62,7 @@
 #define ORC_FLAG_NONFINITE 4u
 
 typedef struct {
-    int32_t kind;     /* 0 = grid, 1 = analytic */
+    int32_t kind;     /* 0 = grid, 1 = analytic, 2 = neural (SIREN) */
     int32_t ideal;    /* 1: E_par := 0 in the RHS */
     int32_t dtype;    /* grid node type: 0 = float64, 1 = float32 */
     int32_t n_r, n_th, n_ph;
@@ -75,6 +77,13 @@ typedef struct {
     double parker_omega; /* rad/s */
     double parker_u;     /* m/s */
     double dipole_m[3];  /* T m^3, B = 3 (m.R) R / r^5 - m / r^3 */
+    /* kind 2: SIREN 3 -> 256 x 4 -> 8 on x = R / siren_rscale; parameters (float64) in
+     * the order W1 [256][3], b1, W2 [256][256] ([out][in]), b2, W3, b3, W4, b4, W5 [8][256],
+     * b5; outputs y_B = B (r/AU)^2 / siren_Bs, y_E = E (r/AU) / siren_Es */
+    const double *siren;
+    double siren_omega0, siren_rscale, siren_Bs, siren_Es;
+    int32_t siren_bf16; /* 1: the values carried between layers are rounded to bfloat16 */
+    int32_t pad1;
 } orc_field;
 
 typedef struct {
@@ -350,10 +359,90 @@ static void analytic_eval(const orc_field *f, const double R[3], orc_fields *o)
     }
 }
 
+/* Neural field: the SIREN's forward pass with three forward-mode tangents t_j = dh/dx_j
+ * per layer, then the unscaling B = Bs y_B (AU/r)^2, E = Es y_E (AU/r) with the product
+ * rule for the Jacobians. bfloat16 rounding (8 significant bits, ties to even) of h and t
+ * after each layer when siren_bf16 is set; the weights are used as given. */
+#define ORC_AU 1.495978707e11
+#define ORC_H 256
+
+static double round_bf16(double a)
+{
+    int e;
+    const double m = frexp(a, &e);
+    return ldexp(nearbyint(m * 256.0), e - 8);
+}
+
+static void siren_eval(const orc_field *f, const double R[3], orc_fields *o)
+{
+    const double *P = f->siren;
+    const double w0 = f->siren_omega0;
+    const int rb = f->siren_bf16;
+    double x[3], h[ORC_H], t[3][ORC_H], hn[ORC_H], tn[3][ORC_H];
+    for (int j = 0; j < 3; ++j)
+        x[j] = R[j] / f->siren_rscale;
+    const double *W1 = P, *b1 = P + 768;
+    for (int q = 0; q < ORC_H; ++q) {
+        const double z = w0 * (W1[3 * q] * x[0] + W1[3 * q + 1] * x[1] + W1[3 * q + 2] * x[2] + b1[q]);
+        h[q] = sin(z);
+        for (int j = 0; j < 3; ++j)
+            t[j][q] = w0 * cos(z) * W1[3 * q + j];
+    }
+    if (rb)
+        for (int q = 0; q < ORC_H; ++q) {
+            h[q] = round_bf16(h[q]);
+            for (int j = 0; j < 3; ++j)
+                t[j][q] = round_bf16(t[j][q]);
+        }
+    for (int k = 2; k <= 4; ++k) {
+        const double *W = P + 1024 + (int64_t)(k - 2) * 65792, *b = W + 65536;
+        for (int q = 0; q < ORC_H; ++q) {
+            double z = b[q], a[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < ORC_H; ++i) {
+                z += W[q * ORC_H + i] * h[i];
+                for (int j = 0; j < 3; ++j)
+                    a[j] += W[q * ORC_H + i] * t[j][i];
+            }
+            hn[q] = sin(z);
+            for (int j = 0; j < 3; ++j)
+                tn[j][q] = cos(z) * a[j];
+        }
+        for (int q = 0; q < ORC_H; ++q) {
+            h[q] = rb ? round_bf16(hn[q]) : hn[q];
+            for (int j = 0; j < 3; ++j)
+                t[j][q] = rb ? round_bf16(tn[j][q]) : tn[j][q];
+        }
+    }
+    const double *W5 = P + 198400, *b5 = P + 200448;
+    double y[8], J[8][3];
+    for (int c = 0; c < 8; ++c) {
+        y[c] = b5[c];
+        J[c][0] = J[c][1] = J[c][2] = 0.0;
+        for (int i = 0; i < ORC_H; ++i) {
+            y[c] += W5[c * ORC_H + i] * h[i];
+            for (int j = 0; j < 3; ++j)
+                J[c][j] += W5[c * ORC_H + i] * t[j][i];
+        }
+    }
+    const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    const double a = ORC_AU / sqrt(r2);
+    for (int c = 0; c < 3; ++c) {
+        o->B[c] = f->siren_Bs * y[c] * a * a;
+        o->E[c] = f->siren_Es * y[3 + c] * a;
+        for (int d = 0; d < 3; ++d) {
+            o->JB[c][d] = f->siren_Bs * a * a * (J[c][d] / f->siren_rscale - 2.0 * y[c] * R[d] / r2);
+            o->JE[c][d] = f->siren_Es * a * (J[3 + c][d] / f->siren_rscale - y[3 + c] * R[d] / r2);
+        }
+    }
+    o->flags = 0;
+}
+
 static void field_eval(const orc_field *f, const double R[3], orc_fields *o)
 {
     if (f->kind == 0)
         grid_eval(f, R, o);
+    else if (f->kind == 2)
+        siren_eval(f, R, o);
     else
         analytic_eval(f, R, o);
 }

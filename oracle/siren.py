@@ -68,6 +68,16 @@ def n_params(n_h: int = N_H, n_out: int = N_OUT) -> int:
     return int(sum(np.prod(sh) for _, sh in shapes(n_h, n_out)))
 
 
+def offset(name: str, n_h: int = N_H, n_out: int = N_OUT) -> int:
+    """Index of the first element of parameter block `name` in the flat vector."""
+    o = 0
+    for nm, sh in shapes(n_h, n_out):
+        if nm == name:
+            return o
+        o += int(np.prod(sh))
+    raise KeyError(name)
+
+
 def unpack(flat, n_h: int = N_H, n_out: int = N_OUT) -> dict:
     flat = np.asarray(flat, dtype=np.float64)
     out, o = {}, 0

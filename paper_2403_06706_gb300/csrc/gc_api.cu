@@ -172,6 +172,13 @@ struct gc_ctx {
     gcn::Neural nn;
     int field_source = GC_FIELD_GRID;
 
+    // split-step push buffers (sources other than the inline grid gather)
+    int64_t split_cap = 0;
+    float *d_req = nullptr, *d_reqR = nullptr, *d_S = nullptr, *d_SR = nullptr;
+    int32_t *d_list = nullptr, *d_count = nullptr;
+    uint64_t field_evals = 0;
+    double field_ms = 0.0;
+
     // launch shape
     int block = 128;
     int grid_waves = 1;      // resident waves of blocks (0: one thread per particle)
@@ -291,7 +298,7 @@ void harvest(gc_ctx *c, const std::vector<Timed> &tl)
     for (const Timed &t : tl) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess)
-            (t.kind == 0 ? c->push_ms : c->sort_ms) += ms;
+            (t.kind == 0 ? c->push_ms : (t.kind == 1 ? c->sort_ms : c->field_ms)) += ms;
     }
     cudaGetLastError(); // a timing that could not be read is not an error of the next call
 }
@@ -571,6 +578,135 @@ int advance_graph(gc_ctx *c, double dt, int64_t n_steps, double lambda_au, bool 
     return GC_OK;
 }
 
+// ----------------------------------------------------------------------------------------
+// Split-step push: for field sources evaluated on many points at once (the neural field),
+// and for the grid evaluated through the same sample buffers (GC_FIELD_GRID_SAMPLED).
+void free_split(gc_ctx *c)
+{
+    void *p[] = {c->d_req, c->d_reqR, c->d_S, c->d_SR, c->d_list, c->d_count};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    c->d_req = c->d_reqR = c->d_S = c->d_SR = nullptr;
+    c->d_list = c->d_count = nullptr;
+    c->split_cap = 0;
+}
+
+int ensure_split(gc_ctx *c)
+{
+    if (c->split_cap >= c->cap && c->d_count) return GC_OK;
+    free_split(c);
+    const size_t n = (size_t)std::max<int64_t>(c->cap, 1);
+    CUDA_TRY(cudaMalloc(&c->d_req, n * 3 * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&c->d_reqR, n * 3 * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&c->d_S, n * gcp::kSampleStride * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&c->d_SR, n * gcp::kSampleStride * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&c->d_list, n * sizeof(int32_t)));
+    CUDA_TRY(cudaMalloc(&c->d_count, sizeof(int32_t)));
+    c->split_cap = (int64_t)n;
+    return GC_OK;
+}
+
+// field samples at R (cap points; the count on the device when n_dev is set)
+int field_samples(gc_ctx *c, const float *R, int64_t cap, const int32_t *n_dev, float *S, LaunchCounts *lc)
+{
+    Timed t;
+    TRY(new_interval(c, 2, nullptr, &t));
+    CUDA_TRY(cudaEventRecord(t.a, c->stream));
+    if (c->field_source == GC_FIELD_SIREN)
+        CUDA_TRY(gcn::neural_field_at(c->nn, R, cap, n_dev, S, gcp::kSampleStride, c->stream));
+    else
+        CUDA_TRY(gcp::launch_grid_samples(c->gh, R, cap, n_dev, S, c->stream));
+    CUDA_TRY(cudaEventRecord(t.b, c->stream));
+    lc->kernels += 1;
+    return GC_OK;
+}
+
+gcp::SplitParams split_params(gc_ctx *c, double dt, double lambda_au)
+{
+    gcp::SplitParams Q{};
+    gcp::PushParams &P = Q.P;
+    P.st = c->st;
+    P.ens = c->d_ens;
+    P.dt = dt;
+    P.t0 = c->t;
+    P.collision_form = c->opt.collision_form;
+    P.no_scatter = c->opt.no_scatter;
+    P.no_rebirth = c->opt.no_rebirth;
+    P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
+    P.seed = c->opt.seed;
+    P.m = c->opt.mass;
+    P.c2 = kC * kC;
+    P.tally_on = c->tally_on ? 1 : 0;
+    P.tally = c->tdev;
+    P.gflags = c->d_flags;
+    P.counters = c->d_counters;
+    Q.req = c->d_req;
+    Q.S = c->d_S;
+    Q.reqR = c->d_reqR;
+    Q.SR = c->d_SR;
+    Q.list = c->d_list;
+    Q.count = c->d_count;
+    Q.g_in_sample = c->field_source == GC_FIELD_SIREN ? 0 : 1;
+    Q.ideal = c->gh.ideal;
+    return Q;
+}
+
+// n_steps steps of the split-step push: per step the predictor requests, two evaluations
+// of all particles, and two evaluations of the restart list
+int split_advance(gc_ctx *c, double dt, int64_t n_steps, double lambda_au, bool *anomaly)
+{
+    TRY(ensure_split(c));
+    gcp::SplitParams Q = split_params(c, dt, lambda_au);
+    const gcp::PhysHost ph = c->phys();
+    cudaStream_t s = c->stream;
+    LaunchCounts lc;
+    const uint64_t coll0 = c->collisions, reb0 = c->rebirths;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        Q.kk = (long long)(k + 1);
+        Q.tally_now = (c->tally_on && ((c->step + k + 1) % c->tdev.cadence == 0)) ? 1 : 0;
+        CUDA_TRY(cudaMemsetAsync(c->d_count, 0, sizeof(int32_t), s));
+        CUDA_TRY(gcp::launch_split(gcp::SPLIT_PRED, ph, Q, s));
+        TRY(field_samples(c, c->d_req, c->n, nullptr, c->d_S, &lc));
+        CUDA_TRY(gcp::launch_split(gcp::SPLIT_CORR, ph, Q, s));
+        TRY(field_samples(c, c->d_req, c->n, nullptr, c->d_S, &lc));
+        CUDA_TRY(gcp::launch_split(gcp::SPLIT_POST, ph, Q, s));
+        TRY(field_samples(c, c->d_reqR, c->n, c->d_count, c->d_SR, &lc));
+        CUDA_TRY(gcp::launch_split(gcp::SPLIT_R2, ph, Q, s));
+        TRY(field_samples(c, c->d_reqR, c->n, c->d_count, c->d_SR, &lc));
+        CUDA_TRY(gcp::launch_split(gcp::SPLIT_R3, ph, Q, s));
+        lc.kernels += 5;
+    }
+    add_counts(c, lc);
+    TRY(collect_status(c, anomaly));
+    c->field_evals += (uint64_t)(2 * c->n * n_steps) + 2 * ((c->collisions - coll0) + (c->rebirths - reb0));
+    return GC_OK;
+}
+
+// redo the field-dependent part of an injection (slots [slot0, slot0 + n_new)) with the
+// selected split-step source: mu_B from |B| at the site and the start-up history
+int split_inject_fix(gc_ctx *c, int64_t slot0, int64_t n_new)
+{
+    TRY(ensure_split(c));
+    gcp::SplitParams Q = split_params(c, c->opt.dt_init, 0.0);
+    Q.slot0 = slot0;
+    Q.n_new = n_new;
+    const gcp::PhysHost ph = c->phys();
+    cudaStream_t s = c->stream;
+    LaunchCounts lc;
+    const int32_t cnt = (int32_t)n_new;
+    CUDA_TRY(gcp::launch_split(gcp::SPLIT_INJ_REQ, ph, Q, s));
+    TRY(field_samples(c, c->d_req, n_new, nullptr, c->d_S, &lc));
+    CUDA_TRY(gcp::launch_split(gcp::SPLIT_INJ_FIX, ph, Q, s));
+    CUDA_TRY(cudaMemcpyAsync(c->d_count, &cnt, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TRY(field_samples(c, c->d_reqR, n_new, c->d_count, c->d_SR, &lc));
+    CUDA_TRY(gcp::launch_split(gcp::SPLIT_R3, ph, Q, s));
+    CUDA_TRY(cudaStreamSynchronize(s)); // the host word cnt is read by the copy above
+    lc.kernels += 3;
+    add_counts(c, lc);
+    c->field_evals += (uint64_t)(2 * n_new);
+    return GC_OK;
+}
+
 void free_tally(gc_ctx *c)
 {
     if (c->d_tally) cudaFree(c->d_tally);
@@ -652,6 +788,7 @@ void gc_destroy(gc_ctx *c)
     if (c->h_clock) cudaFreeHost(c->h_clock);
     gcp::sort_free(c->sortw);
     gcn::neural_free(c->nn);
+    free_split(c);
     for (cudaEvent_t e : c->ev_pool)
         cudaEventDestroy(e);
     delete c;
@@ -804,9 +941,12 @@ int gc_particles_inject(gc_ctx *c, const gc_ensemble_desc *e, int n_ens)
     } else if (c->ids_dense && c->next_id != c->id_lo + (uint32_t)c->n) {
         c->ids_dense = false; // appended ids do not continue the existing range
     }
+    const int64_t slot0 = c->n;
     c->n += total;
     c->st.n = c->n;
     c->next_id += (uint32_t)total;
+    if (total > 0 && c->field_source != GC_FIELD_GRID)
+        TRY(split_inject_fix(c, slot0, total));
     bool anomaly = false;
     TRY(collect_status(c, &anomaly));
     if (anomaly)
@@ -860,7 +1000,9 @@ int gc_advance(gc_ctx *c, double dt, int64_t n_steps, double lambda_au)
         return GC_OK;
     }
     bool anomaly = false;
-    if (c->use_graph) {
+    if (c->field_source != GC_FIELD_GRID) {
+        TRY(split_advance(c, dt, n_steps, lambda_au, &anomaly));
+    } else if (c->use_graph) {
         TRY(advance_graph(c, dt, n_steps, lambda_au, &anomaly));
     } else {
         LaunchCounts lc;
@@ -1239,6 +1381,8 @@ int gc_stats(gc_ctx *c, gc_stats_out *o)
     o->push_ms = c->push_ms;
     o->sorts = c->sorts;
     o->sort_ms = c->sort_ms;
+    o->field_evals = c->field_evals;
+    o->field_ms = c->field_ms;
     return GC_OK;
 }
 
@@ -1373,12 +1517,13 @@ int gc_field_fit(gc_ctx *c, const gc_fit_desc *f, int64_t n_samples, int n_epoch
 int gc_field_select(gc_ctx *c, int source)
 {
     if (!c) return fail(GC_ERR_INVALID, "gc_field_select: null context");
-    if (source != GC_FIELD_GRID && source != GC_FIELD_SIREN)
+    if (source != GC_FIELD_GRID && source != GC_FIELD_SIREN && source != GC_FIELD_GRID_SAMPLED)
         return fail(GC_ERR_INVALID, "gc_field_select: unknown source %d", source);
-    if (source == GC_FIELD_SIREN) {
-        TRY(nn_ready(c, "gc_field_select"));
+    if (source == GC_FIELD_SIREN) TRY(nn_ready(c, "gc_field_select"));
+    if (source != GC_FIELD_GRID) {
         if (c->opt.precision != GC_PREC_FP32_MIXED)
-            return fail(GC_ERR_UNSUPPORTED, "gc_field_select: the neural field runs with GC_PREC_FP32_MIXED only");
+            return fail(GC_ERR_UNSUPPORTED, "gc_field_select: the split-step push runs with GC_PREC_FP32_MIXED only");
+        if (!c->has_field) return fail(GC_ERR_STATE, "gc_field_select: load the grid first");
     }
     drop_graphs(c);
     c->field_source = source;

@@ -68,6 +68,30 @@ struct InjectParams {
     uint32_t *gflags;
 };
 
+// Split-step push: the state machine of the fused push cut at each field evaluation, for
+// field sources that evaluate many points at once (the neural field). Per step:
+//   PRED (all) -> samples -> CORR (all) -> samples -> POST (all; restarts join a list)
+//   -> samples (list) -> R2 (list) -> samples (list) -> R3 (list).
+// INJ_REQ / INJ_FIX redo the field-dependent part of the injection with the samples.
+constexpr int kSampleStride = 36; // B, E, dB, dE (24), g (9), flags (1), pad (2)
+enum SplitKind { SPLIT_PRED = 0, SPLIT_CORR, SPLIT_POST, SPLIT_R2, SPLIT_R3, SPLIT_INJ_REQ, SPLIT_INJ_FIX };
+
+struct SplitParams {
+    PushParams P;          // state, ensembles, physics switches, tallies, counters; P.dt, P.t0
+    float *req;            // [cap][3] request points (m), one per particle slot
+    const float *S;        // [cap][kSampleStride] field samples at req
+    float *reqR;           // [cap][3] requests of the restart list
+    const float *SR;       // samples at reqR
+    int32_t *list;         // slots of the restart list
+    int32_t *count;        // entries in the list (device)
+    int32_t g_in_sample;   // 1: index-space derivatives and g in the sample (grid), 0: Cartesian
+    int32_t tally_now;     // this step ends on a tally sample
+    int32_t ideal;         // drop E_par (ideal MHD field)
+    int32_t pad;
+    long long kk;          // t_new = t0 + kk dt for this step
+    int64_t slot0, n_new;  // injection fix-up: slots [slot0, slot0 + n_new)
+};
+
 } // namespace gcp
 
 // launchers (gc_push.cu)
@@ -86,6 +110,11 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
 cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
                           const InjectParams &p, cudaStream_t s);
 int push_max_blocks_per_sm(int precision, int block);
+// one split-step kernel (FP32 path)
+cudaError_t launch_split(int kind, const PhysHost &ph, const SplitParams &p, cudaStream_t s);
+// grid field samples (FP32 grid) at R (cap x 3, m; count on the device or cap)
+cudaError_t launch_grid_samples(const GridHost &g, const float *R, int64_t cap, const int32_t *n_dev, float *S,
+                                cudaStream_t s);
 // load the push kernels now (a launch inside a stream capture must not trigger loading)
 cudaError_t preload_kernels();
 // message returned by gc_last_error() on the calling thread (gc_api.cu)

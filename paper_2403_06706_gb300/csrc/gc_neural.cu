@@ -427,20 +427,34 @@ cudaError_t neural_set(Neural &nn, const float *params, bool on_device, double o
 
 cudaError_t neural_eval(Neural &nn, const float *x, int64_t n, float *y, float *J, cudaStream_t s)
 {
+    gcs::SirenIn in{x, n, nullptr, 1.0f, (float)nn.r_max};
     gcs::SirenOut o{};
     o.y = y;
     o.J = J;
-    return gcs::siren_eval(nn.net, x, n, o, s);
+    return gcs::siren_eval(nn.net, in, o, s);
 }
 
 cudaError_t neural_field(Neural &nn, const float *x, int64_t n, float *field, cudaStream_t s)
 {
+    gcs::SirenIn in{x, n, nullptr, 1.0f, (float)nn.r_max};
     gcs::SirenOut o{};
     o.field = field;
-    o.r_max = nn.r_max;
+    o.field_stride = 24;
     o.B_scale = nn.B_scale;
     o.E_scale = nn.E_scale;
-    return gcs::siren_eval(nn.net, x, n, o, s);
+    return gcs::siren_eval(nn.net, in, o, s);
+}
+
+cudaError_t neural_field_at(Neural &nn, const float *R, int64_t cap, const int32_t *n_dev, float *samples,
+                            int stride, cudaStream_t s)
+{
+    gcs::SirenIn in{R, cap, n_dev, (float)(1.0 / nn.r_max), 1.0f};
+    gcs::SirenOut o{};
+    o.field = samples;
+    o.field_stride = stride;
+    o.B_scale = nn.B_scale;
+    o.E_scale = nn.E_scale;
+    return gcs::siren_eval(nn.net, in, o, s);
 }
 
 cudaError_t neural_targets(const Neural &nn, const GridRef &g, const float *x, int64_t n, float *t, cudaStream_t s)

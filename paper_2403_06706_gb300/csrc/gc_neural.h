@@ -52,6 +52,10 @@ cudaError_t neural_set(Neural &nn, const float *params, bool on_device, double o
 // raw outputs y (n x 8) and optionally J (n x 8 x 3), or the physical field (n x 24)
 cudaError_t neural_eval(Neural &nn, const float *x, int64_t n, float *y, float *J, cudaStream_t s);
 cudaError_t neural_field(Neural &nn, const float *x, int64_t n, float *field, cudaStream_t s);
+// field samples for the push: R (cap x 3, metres), point count on the device (n_dev, or cap
+// when null), samples with `stride` floats per point
+cudaError_t neural_field_at(Neural &nn, const float *R, int64_t cap, const int32_t *n_dev, float *samples,
+                            int stride, cudaStream_t s);
 // scaled 8-channel targets of the grid interpolant at x (n x 3, scaled by r_max)
 cudaError_t neural_targets(const Neural &nn, const GridRef &g, const float *x, int64_t n, float *t,
                            cudaStream_t s);

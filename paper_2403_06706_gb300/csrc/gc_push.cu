@@ -156,19 +156,315 @@ __device__ __forceinline__ void tally_sample(const TallyDev &T_, const PushParam
 }
 
 // ----------------------------------------------------------------------------------------
-// The per-step work is a loop over evaluation phases so that one copy of the field
-// evaluation serves all of them (instruction-cache footprint):
+// Per-particle state and the four evaluation phases of a step, shared by the fused push
+// (field evaluated inline) and the split-step push (field samples from a buffer).
 //   phase 0  F* at the predictor point (Eq. 5), then the corrector (Eq. 6)
 //   phase 1  F^{n+1} at the corrector point, then free path, rebirth and collision tests
 //   phase 2  F^n of the new state after a rebirth or collision (start-up, Sect. 2.2)
 //   phase 3  F^{n-1} at X^n - dt F^n
-// Phases 2-3 run only for the lanes that restart.
+// Phases 2-3 run only for the particles that restart.
+template <typename T>
+struct PState {
+    using A = typename AccOf<T>::A;
+    A Rx, Ry, Rz, U, S;
+    T mub, F0[4], F1[4], vpar0, hprev, Bm0;
+    double t_birth;
+    uint32_t event, ncoll, flags;
+};
+
+// constants of one particle during a launch
+struct PConst {
+    const EnsDev *E;
+    double lambda, r_in, r_out;
+    float ri2, ro2, lambda_f;
+    int scatter_law;
+    uint32_t id, e;
+};
+
+// predictor / corrector weights of one step
+template <typename T>
+struct StepW {
+    T a0, a1, c0, cs, c1;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_particle(const PushParams &P, int64_t i, PConst &c, PState<T> &s)
+{
+    using Acc = AccOf<T>;
+    const int64_t cap = P.st.cap;
+    c.e = P.st.ens[i];
+    c.E = &P.ens[c.e];
+    c.lambda = P.lambda_override > 0.0 ? P.lambda_override : c.E->lambda;
+    c.r_in = c.E->r_in;
+    c.r_out = c.E->r_out;
+    c.ri2 = c.E->r_in2;
+    c.ro2 = c.E->r_out2;
+    c.lambda_f = P.lambda_override > 0.0 ? (float)P.lambda_override : c.E->lambda_f;
+    c.scatter_law = c.E->scatter_law;
+    c.id = P.st.id[i];
+    s.Rx = Acc::from(P.st.x[i]);
+    s.Ry = Acc::from(P.st.y[i]);
+    s.Rz = Acc::from(P.st.z[i]);
+    s.U = Acc::from(P.st.u[i]);
+    s.S = Acc::from(P.st.s_rem[i]);
+    s.mub = (T)P.st.mub[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        s.F0[k] = (T)P.st.F0[k * cap + i];
+        s.F1[k] = (T)P.st.F1[k * cap + i];
+    }
+    s.vpar0 = (T)P.st.vpar[i];
+    s.hprev = (T)P.st.h_prev[i];
+    s.t_birth = P.st.t_birth[i];
+    s.event = P.st.event[i];
+    s.ncoll = P.st.ncoll[i];
+    s.flags = P.st.flags[i];
+    s.Bm0 = T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_particle(const PushParams &P, int64_t i, const PState<T> &s)
+{
+    using Acc = AccOf<T>;
+    const int64_t cap = P.st.cap;
+    P.st.x[i] = Acc::to(s.Rx);
+    P.st.y[i] = Acc::to(s.Ry);
+    P.st.z[i] = Acc::to(s.Rz);
+    P.st.u[i] = Acc::to(s.U);
+    P.st.s_rem[i] = Acc::to(s.S);
+    P.st.mub[i] = (double)s.mub;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        P.st.F0[k * cap + i] = (double)s.F0[k];
+        P.st.F1[k * cap + i] = (double)s.F1[k];
+    }
+    P.st.vpar[i] = (double)s.vpar0;
+    P.st.h_prev[i] = (double)s.hprev;
+    P.st.t_birth[i] = s.t_birth;
+    P.st.event[i] = s.event;
+    P.st.ncoll[i] = s.ncoll;
+    if (s.flags != P.st.flags[i]) {
+        P.st.flags[i] = s.flags;
+        atomicOr(P.gflags, s.flags);
+    }
+}
+
+// partial stores of the split-step kernels: only what a phase changed, so that the stored
+// doubles of untouched fields keep every bit
+__device__ __forceinline__ void store_flags(const PushParams &P, int64_t i, uint32_t flags)
+{
+    if (flags != P.st.flags[i]) {
+        P.st.flags[i] = flags;
+        atomicOr(P.gflags, flags);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_RU(const PushParams &P, int64_t i, const PState<T> &s)
+{
+    using Acc = AccOf<T>;
+    P.st.x[i] = Acc::to(s.Rx);
+    P.st.y[i] = Acc::to(s.Ry);
+    P.st.z[i] = Acc::to(s.Rz);
+    P.st.u[i] = Acc::to(s.U);
+    store_flags(P, i, s.flags);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_F(const PushParams &P, int64_t i, const PState<T> &s, int which)
+{
+    const int64_t cap = P.st.cap;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (which == 0)
+            P.st.F0[k * cap + i] = (double)s.F0[k];
+        else
+            P.st.F1[k * cap + i] = (double)s.F1[k];
+    }
+    if (which == 0) P.st.vpar[i] = (double)s.vpar0;
+    store_flags(P, i, s.flags);
+}
+
+template <typename T>
+__device__ __forceinline__ StepW<T> step_weights(const StepW<T> &w1, T dtT, T hprev)
+{
+    StepW<T> w = w1;
+    if (hprev != dtT) {
+        // variable step: tau = dt^n / dt^{n-1}; weights (3+tau)/6,
+        // (3+2 tau)/(6(1+tau)), -tau^2/(6(1+tau)) of Eq. 6
+        const T tau = dtT / hprev;
+        w.a0 = dtT * (T(1) + T(0.5) * tau);
+        w.a1 = -dtT * T(0.5) * tau;
+        const T q = dtT / (T(6) * (T(1) + tau));
+        w.c0 = dtT * (T(3) + tau) / T(6);
+        w.cs = q * (T(3) + T(2) * tau);
+        w.c1 = -q * tau * tau;
+    }
+    return w;
+}
+
+// the point (R, gamma v_par) at which phase `phase` evaluates the field
+template <typename T>
+__device__ __forceinline__ void phase_point(int phase, const PState<T> &s, const StepW<T> &w, T dtT, T &px,
+                                            T &py, T &pz, T &pu)
+{
+    using Acc = AccOf<T>;
+    px = Acc::val(s.Rx);
+    py = Acc::val(s.Ry);
+    pz = Acc::val(s.Rz);
+    pu = Acc::val(s.U);
+    if (phase == 0) {
+        px += w.a0 * s.F0[0] + w.a1 * s.F1[0];
+        py += w.a0 * s.F0[1] + w.a1 * s.F1[1];
+        pz += w.a0 * s.F0[2] + w.a1 * s.F1[2];
+        pu += w.a0 * s.F0[3] + w.a1 * s.F1[3];
+    } else if (phase == 3) {
+        px -= dtT * s.F0[0];
+        py -= dtT * s.F0[1];
+        pz -= dtT * s.F0[2];
+        pu -= dtT * s.F0[3];
+    }
+}
+
+// Use the field evaluation Fo (with ax) of phase `phase` for particle slot i; after phase 1
+// a rebirth or a collision sets n_phase = 4. kk: index of the step's end time (t_birth on
+// rebirth).
+template <typename T>
+__device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i, PState<T> &s, const PConst &c,
+                                              const T Fo[4],
+                                              const Aux<T> &ax, const StepW<T> &w, const PushParams &P,
+                                              const Phys<T> &ph, T dtT, double t0, long long kk,
+                                              unsigned &n_coll, unsigned &n_reb)
+{
+    using Acc = AccOf<T>;
+    if (phase == 0) {
+        s.Rx = Acc::add(s.Rx, w.c0 * s.F0[0] + w.cs * Fo[0] + w.c1 * s.F1[0]);
+        s.Ry = Acc::add(s.Ry, w.c0 * s.F0[1] + w.cs * Fo[1] + w.c1 * s.F1[1]);
+        s.Rz = Acc::add(s.Rz, w.c0 * s.F0[2] + w.cs * Fo[2] + w.c1 * s.F1[2]);
+        s.U = Acc::add(s.U, w.c0 * s.F0[3] + w.cs * Fo[3] + w.c1 * s.F1[3]);
+    } else if (phase == 1) {
+        const T px = Acc::val(s.Rx), py = Acc::val(s.Ry), pz = Acc::val(s.Rz);
+        // Sect. 2.3: path length along B in this step
+        const T ds = dtT * (fabs(s.vpar0) + fabs(ax.vpar)) * T(0.5);
+        bool collide = false;
+        if (!P.no_scatter) {
+            if (P.collision_form == 0) {
+                s.S = Acc::add(s.S, -ds);
+                collide = Acc::nonpos(s.S);
+            } else {
+                // the per-step draw of Eq. 9: collide if a < 1 - exp(-ds / lambda)
+                const uint4 wd = draw(c.id, P.seed, s.event++);
+                if constexpr (sizeof(T) == 8)
+                    collide = u53(wd.x, wd.y) < 1.0 - exp(-(double)ds / c.lambda);
+                else
+                    collide = u31(wd.x).u < -expm1f(-(float)ds / c.lambda_f);
+            }
+        }
+        bool reborn = false;
+        if (!P.no_rebirth) {
+            if (sizeof(T) == 8) {
+                const double xx = Acc::to(s.Rx), yy = Acc::to(s.Ry), zz = Acc::to(s.Rz);
+                const double r1 = sqrt(xx * xx + yy * yy + zz * zz);
+                reborn = (r1 < c.r_in || r1 > c.r_out);
+            } else {
+                const float xx = (float)px, yy = (float)py, zz = (float)pz;
+                const float r2 = xx * xx + yy * yy + zz * zz;
+                if (fabsf(r2 - c.ri2) < 1e-5f * c.ri2 || fabsf(r2 - c.ro2) < 1e-5f * c.ro2) {
+                    // near the shell: decide in double from the accumulated position
+                    const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
+                    const double r1 = sqrt(X * X + Y * Y + Z * Z);
+                    reborn = (r1 < c.r_in || r1 > c.r_out);
+                } else {
+                    reborn = (r2 < c.ri2 || r2 > c.ro2);
+                }
+            }
+        }
+        if (reborn) {
+            // Sect. 3: reborn at the injection site with the initial velocity
+            const uint4 wd = draw(c.id, P.seed, s.event++);
+            if constexpr (sizeof(T) == 8) {
+                s.Rx = c.E->R0[0];
+                s.Ry = c.E->R0[1];
+                s.Rz = c.E->R0[2];
+                s.S = -c.lambda * log(u53(wd.z, wd.w));
+            } else {
+                s.Rx = df{c.E->R0_hi[0], c.E->R0_lo[0]};
+                s.Ry = df{c.E->R0_hi[1], c.E->R0_lo[1]};
+                s.Rz = df{c.E->R0_hi[2], c.E->R0_lo[2]};
+                s.S = df{c.lambda_f * neg_log_u(u31(wd.z)), 0.0f};
+            }
+            s.U = Acc::from(P.st.u_inj[i]);
+            s.mub = (T)P.st.mub_inj[i];
+            s.ncoll = 0;
+            s.t_birth = step_time(t0, kk, P.dt);
+            ++n_reb;
+            n_phase = 4;
+        } else if (collide) {
+            // inertial-frame elastic collision: |p| kept, B at R^{n+1}; new pitch
+            // cosine from Eq. 10 (mu = 1 - 2a) or Eq. 12 (mu = +-sqrt(a))
+            const uint4 wd = draw(c.id, P.seed, s.event++);
+            if constexpr (sizeof(T) == 8) {
+                const double a = u53(wd.x, wd.y);
+                const double mu_new = (c.scatter_law == 0) ? 1.0 - 2.0 * a : ((wd.x & 1u) ? -sqrt(a) : sqrt(a));
+                const double Bm = (double)ax.Bm;
+                const double uu = Acc::to(s.U);
+                const double pm2 = uu * uu + 2.0 * (double)s.mub * Bm / P.m;
+                const double pm = sqrt(pm2);
+                s.U = mu_new * pm;
+                s.mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
+                if (P.collision_form == 0)
+                    s.S = -c.lambda * log(u53(wd.z, wd.w));
+            } else {
+                // sin^2 of the new pitch angle without cancellation: 4 a (1 - a)
+                // for Eq. 10 (mu = (1 - a) - a), 1 - a for Eq. 12 (mu^2 = a)
+                const UPair ua = u31(wd.x);
+                float mu_new, sin2;
+                if (c.scatter_law == 0) {
+                    mu_new = ua.ub - ua.u;
+                    sin2 = 4.0f * ua.u * ua.ub;
+                } else {
+                    mu_new = (wd.x & 1u) ? -sqrtf(ua.u) : sqrtf(ua.u);
+                    sin2 = ua.ub;
+                }
+                const float Bm = (float)ax.Bm;
+                const float uu = (float)Acc::val(s.U);
+                const float pm2 = uu * uu + 2.0f * (float)s.mub * Bm * (float)ph.inv_m;
+                s.U = df{mu_new * sqrtf(pm2), 0.0f};
+                s.mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
+                if (P.collision_form == 0)
+                    s.S = df{c.lambda_f * neg_log_u(u31(wd.z)), 0.0f};
+            }
+            ++s.ncoll;
+            ++n_coll;
+            n_phase = 4;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s.F1[k] = s.F0[k];
+                s.F0[k] = Fo[k];
+            }
+            s.vpar0 = ax.vpar;
+            s.Bm0 = ax.Bm;
+        }
+    } else if (phase == 2) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            s.F0[k] = Fo[k];
+        s.vpar0 = ax.vpar;
+        s.Bm0 = ax.Bm;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            s.F1[k] = Fo[k];
+    }
+}
+// ----------------------------------------------------------------------------------------
+// Fused push: one thread owns a particle for all the steps of a launch and evaluates the
+// grid field inline (one copy of the evaluation serves all phases: instruction cache).
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                    const PushParams P)
 {
-    using Acc = AccOf<T>;
-    using A = typename Acc::A;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned n_coll = 0, n_reb = 0;
     const T dtT = (T)P.dt;
@@ -179,35 +475,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
         step0 = (int64_t)P.clock[1] + P.kbase;
     }
     // Eq. 5-6 weights at tau = 1: 3/2, -1/2 (AB2) and 2/3, 5/12, -1/12 (AM3)
-    const T a0_1 = dtT * T(1.5), a1_1 = dtT * T(-0.5);
-    const T c0_1 = dtT * T(2.0 / 3.0), cs_1 = dtT * T(5.0 / 12.0), c1_1 = dtT * T(-1.0 / 12.0);
+    const StepW<T> w1 = {dtT * T(1.5), dtT * T(-0.5), dtT * T(2.0 / 3.0), dtT * T(5.0 / 12.0),
+                         dtT * T(-1.0 / 12.0)};
 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.st.n; i += stride) {
-        const int64_t cap = P.st.cap;
-        const uint32_t e = P.st.ens[i];
-        const EnsDev &E = P.ens[e];
-        const double lambda = P.lambda_override > 0.0 ? P.lambda_override : E.lambda;
-        const double r_in = E.r_in, r_out = E.r_out;
-        const float ri2 = E.r_in2, ro2 = E.r_out2;
-        const float lambda_f = P.lambda_override > 0.0 ? (float)P.lambda_override : E.lambda_f;
-        const int scatter_law = E.scatter_law;
-        const uint32_t id = P.st.id[i];
-
-        A Rx = Acc::from(P.st.x[i]), Ry = Acc::from(P.st.y[i]), Rz = Acc::from(P.st.z[i]);
-        A U = Acc::from(P.st.u[i]);
-        A S = Acc::from(P.st.s_rem[i]);
-        T mub = (T)P.st.mub[i];
-        T F0[4], F1[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            F0[c] = (T)P.st.F0[c * cap + i];
-            F1[c] = (T)P.st.F1[c * cap + i];
-        }
-        T vpar0 = (T)P.st.vpar[i];
-        T hprev = (T)P.st.h_prev[i];
-        double t_birth = P.st.t_birth[i];
-        uint32_t event = P.st.event[i], ncoll = P.st.ncoll[i], flags = P.st.flags[i];
-        T Bm0 = T(0);
+        PConst c;
+        PState<T> s;
+        load_particle(P, i, c, s);
         int next_tally = -1;
         if (P.tally_on) {
             const int64_t K = P.tally.cadence;
@@ -215,191 +489,31 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
         }
 
         for (int k = 0; k < P.n_steps; ++k) {
-            T a0 = a0_1, a1 = a1_1, c0 = c0_1, cs = cs_1, c1 = c1_1;
-            if (hprev != dtT) {
-                // variable step: tau = dt^n / dt^{n-1}; weights (3+tau)/6,
-                // (3+2 tau)/(6(1+tau)), -tau^2/(6(1+tau)) of Eq. 6
-                const T tau = dtT / hprev;
-                a0 = dtT * (T(1) + T(0.5) * tau);
-                a1 = -dtT * T(0.5) * tau;
-                const T w = dtT / (T(6) * (T(1) + tau));
-                c0 = dtT * (T(3) + tau) / T(6);
-                cs = w * (T(3) + T(2) * tau);
-                c1 = -w * tau * tau;
-            }
+            const StepW<T> w = step_weights(w1, dtT, s.hprev);
             int n_phase = 2;
 #pragma unroll 1
             for (int phase = 0; phase < n_phase; ++phase) {
-                T px = Acc::val(Rx), py = Acc::val(Ry), pz = Acc::val(Rz), pu = Acc::val(U);
-                if (phase == 0) {
-                    px += a0 * F0[0] + a1 * F1[0];
-                    py += a0 * F0[1] + a1 * F1[1];
-                    pz += a0 * F0[2] + a1 * F1[2];
-                    pu += a0 * F0[3] + a1 * F1[3];
-                } else if (phase == 3) {
-                    px -= dtT * F0[0];
-                    py -= dtT * F0[1];
-                    pz -= dtT * F0[2];
-                    pu -= dtT * F0[3];
-                }
+                T px, py, pz, pu;
+                phase_point(phase, s, w, dtT, px, py, pz, pu);
                 T Fo[4];
                 Aux<T> ax;
-                flags |= eval_F(gm, ph, px, py, pz, pu, mub, Fo, ax);
-
-                if (phase == 0) {
-                    Rx = Acc::add(Rx, c0 * F0[0] + cs * Fo[0] + c1 * F1[0]);
-                    Ry = Acc::add(Ry, c0 * F0[1] + cs * Fo[1] + c1 * F1[1]);
-                    Rz = Acc::add(Rz, c0 * F0[2] + cs * Fo[2] + c1 * F1[2]);
-                    U = Acc::add(U, c0 * F0[3] + cs * Fo[3] + c1 * F1[3]);
-                } else if (phase == 1) {
-                    // Sect. 2.3: path length along B in this step
-                    const T ds = dtT * (fabs(vpar0) + fabs(ax.vpar)) * T(0.5);
-                    bool collide = false;
-                    if (!P.no_scatter) {
-                        if (P.collision_form == 0) {
-                            S = Acc::add(S, -ds);
-                            collide = Acc::nonpos(S);
-                        } else {
-                            // the per-step draw of Eq. 9: collide if a < 1 - exp(-ds / lambda)
-                            const uint4 wd = draw(id, P.seed, event++);
-                            if constexpr (sizeof(T) == 8)
-                                collide = u53(wd.x, wd.y) < 1.0 - exp(-(double)ds / lambda);
-                            else
-                                collide = u31(wd.x).u < -expm1f(-(float)ds / lambda_f);
-                        }
-                    }
-                    bool reborn = false;
-                    if (!P.no_rebirth) {
-                        if (sizeof(T) == 8) {
-                            const double xx = Acc::to(Rx), yy = Acc::to(Ry), zz = Acc::to(Rz);
-                            const double r1 = sqrt(xx * xx + yy * yy + zz * zz);
-                            reborn = (r1 < r_in || r1 > r_out);
-                        } else {
-                            const float xx = (float)px, yy = (float)py, zz = (float)pz;
-                            const float r2 = xx * xx + yy * yy + zz * zz;
-                            if (fabsf(r2 - ri2) < 1e-5f * ri2 || fabsf(r2 - ro2) < 1e-5f * ro2) {
-                                // near the shell: decide in double from the accumulated position
-                                const double X = Acc::to(Rx), Y = Acc::to(Ry), Z = Acc::to(Rz);
-                                const double r1 = sqrt(X * X + Y * Y + Z * Z);
-                                reborn = (r1 < r_in || r1 > r_out);
-                            } else {
-                                reborn = (r2 < ri2 || r2 > ro2);
-                            }
-                        }
-                    }
-                    if (reborn) {
-                        // Sect. 3: reborn at the injection site with the initial velocity
-                        const uint4 wd = draw(id, P.seed, event++);
-                        if constexpr (sizeof(T) == 8) {
-                            Rx = E.R0[0];
-                            Ry = E.R0[1];
-                            Rz = E.R0[2];
-                            S = -lambda * log(u53(wd.z, wd.w));
-                        } else {
-                            Rx = df{E.R0_hi[0], E.R0_lo[0]};
-                            Ry = df{E.R0_hi[1], E.R0_lo[1]};
-                            Rz = df{E.R0_hi[2], E.R0_lo[2]};
-                            S = df{lambda_f * neg_log_u(u31(wd.z)), 0.0f};
-                        }
-                        U = Acc::from(P.st.u_inj[i]);
-                        mub = (T)P.st.mub_inj[i];
-                        ncoll = 0;
-                        t_birth = step_time(t0, (long long)(P.kbase + k + 1), P.dt);
-                        ++n_reb;
-                        n_phase = 4;
-                    } else if (collide) {
-                        // inertial-frame elastic collision: |p| kept, B at R^{n+1}; new pitch
-                        // cosine from Eq. 10 (mu = 1 - 2a) or Eq. 12 (mu = +-sqrt(a))
-                        const uint4 wd = draw(id, P.seed, event++);
-                        if constexpr (sizeof(T) == 8) {
-                            const double a = u53(wd.x, wd.y);
-                            const double mu_new = (scatter_law == 0) ? 1.0 - 2.0 * a
-                                                                     : ((wd.x & 1u) ? -sqrt(a) : sqrt(a));
-                            const double Bm = (double)ax.Bm;
-                            const double uu = Acc::to(U);
-                            const double pm2 = uu * uu + 2.0 * (double)mub * Bm / P.m;
-                            const double pm = sqrt(pm2);
-                            U = mu_new * pm;
-                            mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
-                            if (P.collision_form == 0)
-                                S = -lambda * log(u53(wd.z, wd.w));
-                        } else {
-                            // sin^2 of the new pitch angle without cancellation: 4 a (1 - a)
-                            // for Eq. 10 (mu = (1 - a) - a), 1 - a for Eq. 12 (mu^2 = a)
-                            const UPair ua = u31(wd.x);
-                            float mu_new, sin2;
-                            if (scatter_law == 0) {
-                                mu_new = ua.ub - ua.u;
-                                sin2 = 4.0f * ua.u * ua.ub;
-                            } else {
-                                mu_new = (wd.x & 1u) ? -sqrtf(ua.u) : sqrtf(ua.u);
-                                sin2 = ua.ub;
-                            }
-                            const float Bm = (float)ax.Bm;
-                            const float uu = (float)Acc::val(U);
-                            const float pm2 = uu * uu + 2.0f * (float)mub * Bm * (float)ph.inv_m;
-                            U = df{mu_new * sqrtf(pm2), 0.0f};
-                            mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
-                            if (P.collision_form == 0)
-                                S = df{lambda_f * neg_log_u(u31(wd.z)), 0.0f};
-                        }
-                        ++ncoll;
-                        ++n_coll;
-                        n_phase = 4;
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            F1[c] = F0[c];
-                            F0[c] = Fo[c];
-                        }
-                        vpar0 = ax.vpar;
-                        Bm0 = ax.Bm;
-                    }
-                } else if (phase == 2) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        F0[c] = Fo[c];
-                    vpar0 = ax.vpar;
-                    Bm0 = ax.Bm;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        F1[c] = Fo[c];
-                }
+                s.flags |= eval_F(gm, ph, px, py, pz, pu, s.mub, Fo, ax);
+                phase_consume(phase, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, t0, (long long)(P.kbase + k + 1),
+                              n_coll, n_reb);
             }
-            hprev = dtT;
-            if (!(m_finite(Acc::val(Rx)) && m_finite(Acc::val(U)) && m_finite(F0[0])))
-                flags |= FLAG_NONFINITE;
+            s.hprev = dtT;
+            if (!(m_finite(AccOf<T>::val(s.Rx)) && m_finite(AccOf<T>::val(s.U)) && m_finite(s.F0[0])))
+                s.flags |= FLAG_NONFINITE;
 
             if (k == next_tally) {
                 next_tally += P.tally.cadence;
                 const double t_new = step_time(t0, (long long)(P.kbase + k + 1), P.dt);
-                tally_sample<T>(P.tally, P, ph, e, Acc::val(Rx), Acc::val(Ry), Acc::val(Rz), Acc::val(U),
-                                mub, Bm0, t_new - t_birth, ncoll,
-                                t_birth >= P.tally.t_start && (int)e < P.tally.n_ens);
+                tally_sample<T>(P.tally, P, ph, c.e, AccOf<T>::val(s.Rx), AccOf<T>::val(s.Ry), AccOf<T>::val(s.Rz),
+                                AccOf<T>::val(s.U), s.mub, s.Bm0, t_new - s.t_birth, s.ncoll,
+                                s.t_birth >= P.tally.t_start && (int)c.e < P.tally.n_ens);
             }
         }
-
-        P.st.x[i] = Acc::to(Rx);
-        P.st.y[i] = Acc::to(Ry);
-        P.st.z[i] = Acc::to(Rz);
-        P.st.u[i] = Acc::to(U);
-        P.st.s_rem[i] = Acc::to(S);
-        P.st.mub[i] = (double)mub;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            P.st.F0[c * cap + i] = (double)F0[c];
-            P.st.F1[c * cap + i] = (double)F1[c];
-        }
-        P.st.vpar[i] = (double)vpar0;
-        P.st.h_prev[i] = (double)hprev;
-        P.st.t_birth[i] = t_birth;
-        P.st.event[i] = event;
-        P.st.ncoll[i] = ncoll;
-        if (flags != P.st.flags[i]) {
-            P.st.flags[i] = flags;
-            atomicOr(P.gflags, flags);
-        }
+        store_particle(P, i, s);
     }
     // counters: one atomic per warp
     const unsigned mask = __activemask();
@@ -413,6 +527,29 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
 
 // ----------------------------------------------------------------------------------------
 // Injection (Sect. 3): site, mu0 and energy draws (Philox events 0 and 1), start-up history.
+struct InjDraw {
+    double mu0, pm; // pitch cosine and momentum magnitude |p| / m = gamma v
+    uint4 w0;       // event 0 (mu0 and the first free path)
+};
+
+__device__ __forceinline__ InjDraw inj_draw(const EnsDev &E, uint32_t id, uint32_t seed, double m, double c2)
+{
+    InjDraw d;
+    d.w0 = draw(id, seed, 0u);
+    const uint4 w1 = draw(id, seed, 1u);
+    d.mu0 = (E.mu_law == 1) ? 1.0 : u53(d.w0.x, d.w0.y);
+    double Ek = E.E0;
+    if (E.energy_law == 1) {
+        const double a = 1.0 - E.E_index;
+        const double uu = u53(w1.x, w1.y);
+        Ek = pow(pow(E.E_lo, a) + uu * (pow(E.E_hi, a) - pow(E.E_lo, a)), 1.0 / a);
+    }
+    const double mc2 = m * c2;
+    const double gam = 1.0 + Ek / mc2;
+    d.pm = sqrt(c2) * sqrt(gam * gam - 1.0);
+    return d;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                      const InjectParams P)
@@ -426,18 +563,9 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
         ++e;
     const EnsDev &E = P.ens[e];
     const uint32_t id = P.id0 + (uint32_t)j;
-    const uint4 w0 = draw(id, P.seed, 0u);
-    const uint4 w1 = draw(id, P.seed, 1u);
-    const double mu0 = (E.mu_law == 1) ? 1.0 : u53(w0.x, w0.y);
-    double Ek = E.E0;
-    if (E.energy_law == 1) {
-        const double a = 1.0 - E.E_index;
-        const double uu = u53(w1.x, w1.y);
-        Ek = pow(pow(E.E_lo, a) + uu * (pow(E.E_hi, a) - pow(E.E_lo, a)), 1.0 / a);
-    }
-    const double mc2 = P.m * P.c2;
-    const double gam = 1.0 + Ek / mc2;
-    const double pm = sqrt(P.c2) * sqrt(gam * gam - 1.0);
+    const InjDraw d = inj_draw(E, id, P.seed, P.m, P.c2);
+    const double mu0 = d.mu0, pm = d.pm;
+    const uint4 w0 = d.w0;
     Sample<T> s;
     gather(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], s);
     const double Bm = (double)m_sqrt(dot3(s.B, s.B));
@@ -475,6 +603,202 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
     P.st.flags[i] = flags;
     if (flags)
         atomicOr(P.gflags, flags);
+}
+
+// ----------------------------------------------------------------------------------------
+// Split-step push (FP32 path). Each kernel advances every particle (or every entry of the
+// restart list) by one evaluation phase, using the field samples of its request points.
+__device__ __forceinline__ void load_sample(const float *__restrict__ S, int64_t k, int g_in, Sample<float> &s)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(S + k * kSampleStride);
+    float v[36];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const float4 t = __ldg(q + j);
+        v[4 * j] = t.x;
+        v[4 * j + 1] = t.y;
+        v[4 * j + 2] = t.z;
+        v[4 * j + 3] = t.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s.B[c] = v[c];
+        s.E[c] = v[3 + c];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            s.dB[d][c] = v[6 + 3 * d + c];
+            s.dE[d][c] = v[15 + 3 * d + c];
+            s.g[d][c] = g_in ? v[24 + 3 * d + c] : (d == c ? 1.0f : 0.0f);
+        }
+    s.flags = g_in ? __float_as_uint(v[33]) : 0u;
+}
+
+__device__ __forceinline__ void put_point(float *R, int64_t k, float x, float y, float z)
+{
+    R[3 * k] = x;
+    R[3 * k + 1] = y;
+    R[3 * k + 2] = z;
+}
+
+__device__ __forceinline__ void flush_counters(const PushParams &P, unsigned n_coll, unsigned n_reb)
+{
+    const unsigned mask = __activemask();
+    const unsigned c_sum = __reduce_add_sync(mask, n_coll);
+    const unsigned r_sum = __reduce_add_sync(mask, n_reb);
+    if ((threadIdx.x & 31u) == (unsigned)(__ffs(mask) - 1)) {
+        if (c_sum) atomicAdd(P.counters + 0, (unsigned long long)c_sum);
+        if (r_sum) atomicAdd(P.counters + 1, (unsigned long long)r_sum);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128) split_kernel(const Phys<float> ph, const SplitParams Q)
+{
+    using Acc = AccOf<float>;
+    const PushParams &P = Q.P;
+    const float dtT = (float)P.dt;
+    const StepW<float> w1 = {dtT * 1.5f, dtT * -0.5f, dtT * (float)(2.0 / 3.0), dtT * (float)(5.0 / 12.0),
+                             dtT * (float)(-1.0 / 12.0)};
+    const bool on_list = (KIND == SPLIT_R2 || KIND == SPLIT_R3);
+    int64_t n = P.st.n;
+    if (on_list) n = *Q.count;
+    if (KIND == SPLIT_INJ_REQ || KIND == SPLIT_INJ_FIX) n = Q.n_new;
+    unsigned n_coll = 0, n_reb = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        if constexpr (KIND == SPLIT_INJ_REQ) {
+            const EnsDev &E = P.ens[P.st.ens[Q.slot0 + k]];
+            put_point(Q.req, k, (float)E.R0[0], (float)E.R0[1], (float)E.R0[2]);
+            continue;
+        }
+        const int64_t i = on_list ? (int64_t)Q.list[k] : (KIND == SPLIT_INJ_FIX ? Q.slot0 + k : k);
+        PConst c;
+        PState<float> s;
+        load_particle(P, i, c, s);
+        const StepW<float> w = step_weights(w1, dtT, s.hprev);
+        Sample<float> smp;
+        float Fo[4];
+        Aux<float> ax;
+        float px, py, pz, pu;
+        int n_phase = 2;
+        if constexpr (KIND == SPLIT_PRED) {
+            phase_point(0, s, w, dtT, px, py, pz, pu);
+            put_point(Q.req, i, px, py, pz);
+            continue;
+        } else if constexpr (KIND == SPLIT_CORR) {
+            phase_point(0, s, w, dtT, px, py, pz, pu);
+            load_sample(Q.S, i, Q.g_in_sample, smp);
+            s.flags |= smp.flags;
+            rhs(smp, ph, Q.ideal, pu, s.mub, Fo, ax);
+            phase_consume(0, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
+            put_point(Q.req, i, Acc::val(s.Rx), Acc::val(s.Ry), Acc::val(s.Rz));
+            store_RU(P, i, s);
+        } else if constexpr (KIND == SPLIT_POST) {
+            phase_point(1, s, w, dtT, px, py, pz, pu);
+            load_sample(Q.S, i, Q.g_in_sample, smp);
+            s.flags |= smp.flags;
+            rhs(smp, ph, Q.ideal, pu, s.mub, Fo, ax);
+            phase_consume(1, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
+            s.hprev = dtT;
+            if (n_phase == 4) {
+                const int32_t slot = atomicAdd(Q.count, 1);
+                Q.list[slot] = (int32_t)i;
+                put_point(Q.reqR, slot, Acc::val(s.Rx), Acc::val(s.Ry), Acc::val(s.Rz));
+            } else {
+                if (!(m_finite(Acc::val(s.Rx)) && m_finite(Acc::val(s.U)) && m_finite(s.F0[0])))
+                    s.flags |= FLAG_NONFINITE;
+                if (Q.tally_now) {
+                    const double t_new = step_time(P.t0, Q.kk, P.dt);
+                    tally_sample<float>(P.tally, P, ph, c.e, Acc::val(s.Rx), Acc::val(s.Ry), Acc::val(s.Rz),
+                                        Acc::val(s.U), s.mub, s.Bm0, t_new - s.t_birth, s.ncoll,
+                                        s.t_birth >= P.tally.t_start && (int)c.e < P.tally.n_ens);
+                }
+            }
+            store_particle(P, i, s);
+        } else if constexpr (KIND == SPLIT_R2) {
+            phase_point(2, s, w, dtT, px, py, pz, pu);
+            load_sample(Q.SR, k, Q.g_in_sample, smp);
+            s.flags |= smp.flags;
+            rhs(smp, ph, Q.ideal, pu, s.mub, Fo, ax);
+            phase_consume(2, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
+            if (Q.tally_now) {
+                const double t_new = step_time(P.t0, Q.kk, P.dt);
+                tally_sample<float>(P.tally, P, ph, c.e, Acc::val(s.Rx), Acc::val(s.Ry), Acc::val(s.Rz),
+                                    Acc::val(s.U), s.mub, s.Bm0, t_new - s.t_birth, s.ncoll,
+                                    s.t_birth >= P.tally.t_start && (int)c.e < P.tally.n_ens);
+            }
+            phase_point(3, s, w, dtT, px, py, pz, pu);
+            put_point(Q.reqR, k, px, py, pz);
+            store_F(P, i, s, 0);
+        } else if constexpr (KIND == SPLIT_R3) {
+            phase_point(3, s, w, dtT, px, py, pz, pu);
+            load_sample(Q.SR, k, Q.g_in_sample, smp);
+            s.flags |= smp.flags;
+            rhs(smp, ph, Q.ideal, pu, s.mub, Fo, ax);
+            phase_consume(3, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
+            if (!(m_finite(Acc::val(s.Rx)) && m_finite(Acc::val(s.U)) && m_finite(s.F0[0])))
+                s.flags |= FLAG_NONFINITE;
+            store_F(P, i, s, 1);
+        } else if constexpr (KIND == SPLIT_INJ_FIX) {
+            // the injection's field-dependent part with this source: mu_B from |B| at the
+            // site, F^n there, and the F^{n-1} request at X^n - dt F^n (Sect. 2.2)
+            const InjDraw d = inj_draw(*c.E, c.id, P.seed, P.m, P.c2);
+            load_sample(Q.S, k, Q.g_in_sample, smp);
+            s.flags |= smp.flags;
+            const double Bm = (double)m_sqrt(dot3(smp.B, smp.B));
+            const double u = d.mu0 * d.pm;
+            const double mub = (1.0 - d.mu0 * d.mu0) * d.pm * d.pm * P.m / (2.0 * Bm);
+            s.U = Acc::from(u);
+            s.mub = (float)mub;
+            rhs(smp, ph, Q.ideal, (float)u, (float)mub, Fo, ax);
+            phase_consume(2, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
+            Q.list[k] = (int32_t)i;
+            phase_point(3, s, w, dtT, px, py, pz, pu);
+            put_point(Q.reqR, k, px, py, pz);
+            P.st.u[i] = u;
+            P.st.mub[i] = mub;
+            P.st.u_inj[i] = u;
+            P.st.mub_inj[i] = mub;
+            store_F(P, i, s, 0);
+        }
+    }
+    if (KIND == SPLIT_POST) flush_counters(P, n_coll, n_reb);
+}
+
+// grid samples in the split-step layout (Sample fields, index-space derivatives with g)
+__global__ void __launch_bounds__(128) grid_sample_kernel(const GridMeta<float> gm, const float *__restrict__ R,
+                                                          int64_t cap, const int32_t *n_dev, float *__restrict__ S)
+{
+    int64_t n = cap;
+    if (n_dev) n = *n_dev < cap ? *n_dev : cap;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        Sample<float> s;
+        gather(gm, R[3 * k], R[3 * k + 1], R[3 * k + 2], s);
+        float v[36];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = s.B[c];
+            v[3 + c] = s.E[c];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[6 + 3 * d + c] = s.dB[d][c];
+                v[15 + 3 * d + c] = s.dE[d][c];
+                v[24 + 3 * d + c] = s.g[d][c];
+            }
+        v[33] = __uint_as_float(s.flags);
+        v[34] = 0.f;
+        v[35] = 0.f;
+        float4 *q = reinterpret_cast<float4 *>(S + k * kSampleStride);
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            q[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -529,6 +853,41 @@ cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
         inject_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
     else
         inject_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(int kind, const PhysHost &ph, const SplitParams &p, cudaStream_t s)
+{
+    const Phys<float> q = make_phys<float>(ph);
+    const int block = 128;
+    int64_t n = p.P.st.n;
+    if (kind == SPLIT_R2 || kind == SPLIT_R3) n = p.P.st.n; // list length known on the device only
+    if (kind == SPLIT_INJ_REQ || kind == SPLIT_INJ_FIX) n = p.n_new;
+    int64_t blocks = (n + block - 1) / block;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    cudaGetLastError();
+    switch (kind) {
+    case SPLIT_PRED: split_kernel<SPLIT_PRED><<<(int)blocks, block, 0, s>>>(q, p); break;
+    case SPLIT_CORR: split_kernel<SPLIT_CORR><<<(int)blocks, block, 0, s>>>(q, p); break;
+    case SPLIT_POST: split_kernel<SPLIT_POST><<<(int)blocks, block, 0, s>>>(q, p); break;
+    case SPLIT_R2: split_kernel<SPLIT_R2><<<(int)blocks, block, 0, s>>>(q, p); break;
+    case SPLIT_R3: split_kernel<SPLIT_R3><<<(int)blocks, block, 0, s>>>(q, p); break;
+    case SPLIT_INJ_REQ: split_kernel<SPLIT_INJ_REQ><<<(int)blocks, block, 0, s>>>(q, p); break;
+    case SPLIT_INJ_FIX: split_kernel<SPLIT_INJ_FIX><<<(int)blocks, block, 0, s>>>(q, p); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_samples(const GridHost &g, const float *R, int64_t cap, const int32_t *n_dev, float *S,
+                                cudaStream_t s)
+{
+    int64_t blocks = (cap + 127) / 128;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    cudaGetLastError();
+    grid_sample_kernel<<<(int)blocks, 128, 0, s>>>(make_meta<float>(g), R, cap, n_dev, S);
     return cudaGetLastError();
 }
 

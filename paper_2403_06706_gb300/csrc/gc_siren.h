@@ -38,18 +38,31 @@ struct SirenNet {
     CUtensorMap map_wh, map_w5;
 };
 
-// Output of a fused evaluation. Raw mode: y (n x 8) and, if J is set, J (n x 8 x 3) =
-// dy/dx. Field mode (field != null): the physical field for the push, see gc_siren_eval.cu.
+// Output of a fused evaluation. Raw mode (field == null): y (n x 8) and, if J is set,
+// J (n x 8 x 3) = dy/dx. Field mode: per point `field_stride` floats starting with the
+// physical B (3), E (3), dB[d][c] = dB_c/dR_d (9), dE[d][c] (9), from the product rule on
+// B = B_scale y_B (1 AU / r)^2, E = E_scale y_E (1 AU / r).
 struct SirenOut {
     float *y, *J;
     float *field;
-    double r_max, B_scale, E_scale; // field mode: x = R / r_max, unscaling of Eq. (targets)
+    int field_stride;
+    double B_scale, E_scale;
+};
+
+// Inputs: n points p (n x 3); the network sees x = x_scale p and the field mode's physical
+// position is R = pos_scale p. n_dev, if set, holds the point count on the device (read by
+// the kernel; n is then the capacity of the buffers).
+struct SirenIn {
+    const float *p;
+    int64_t n;
+    const int32_t *n_dev;
+    float x_scale, pos_scale;
 };
 
 // build the two tensor maps of net (Wh and W5p must be set)
 cudaError_t siren_maps(SirenNet &net);
-// evaluate the network (and its Jacobian) at n points x (n x 3, device)
-cudaError_t siren_eval(const SirenNet &net, const float *x, int64_t n, const SirenOut &out, cudaStream_t s);
+// evaluate the network (and its Jacobian) at the input points (device)
+cudaError_t siren_eval(const SirenNet &net, const SirenIn &in, const SirenOut &out, cudaStream_t s);
 // CTAs of the fused evaluation per launch (one per SM)
 int siren_eval_grid(int64_t n);
 } // namespace gcs

@@ -49,8 +49,7 @@ constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + 1024 + 128;
 
 struct EvalParams {
     const float *P;  // master parameters
-    const float *x;  // n x 3
-    int64_t n;
+    SirenIn in;
     SirenOut out;
     float omega0;
     int *err;        // error word (device), set when a wait runs out
@@ -119,7 +118,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n_tiles = (p.n + kPts - 1) / kPts;
+    int64_t n_pts = p.in.n;
+    if (p.in.n_dev) {
+        const int64_t nd = *p.in.n_dev;
+        n_pts = nd < n_pts ? (nd > 0 ? nd : 0) : n_pts;
+    }
+    const int64_t n_tiles = (n_pts + kPts - 1) / kPts;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStagesW; ++s) {
@@ -258,10 +262,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int e = 0; e < 2; ++e) {
                     const int64_t P = base + 2 * p2 + e;
                     float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-                    if (P < p.n) {
-                        x0 = __ldg(p.x + 3 * P);
-                        x1 = __ldg(p.x + 3 * P + 1);
-                        x2 = __ldg(p.x + 3 * P + 2);
+                    if (P < n_pts) {
+                        x0 = __ldg(p.in.p + 3 * P) * p.in.x_scale;
+                        x1 = __ldg(p.in.p + 3 * P + 1) * p.in.x_scale;
+                        x2 = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
                     }
                     const float z = w0 * fmaf(w1x, x0, fmaf(w1y, x1, fmaf(w1z, x2, b1)));
                     float sn, cs;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int q = pr & 3;
             const int64_t P = base + (pr >> 2);
             if (p.out.field == nullptr) {
-                if (P < p.n) {
+                if (P < n_pts) {
                     if (q == 0) {
 #pragma unroll
                         for (int o = 0; o < 8; ++o)
@@ -334,25 +338,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             } else {
-                // physical field: B = B_s y_B (AU/r)^2, E = E_s y_E (AU/r) at R = r_max x;
-                // gradients by the product rule with d/dR = (1/r_max) d/dx
+                // physical field: B = B_s y_B (AU/r)^2, E = E_s y_E (AU/r) at R = pos_scale p;
+                // gradients by the product rule with d/dR = (x_scale / pos_scale) d/dx
                 const unsigned full_mask = 0xffffffffu;
                 const int src = lane & ~3;
                 float yv[6];
 #pragma unroll
                 for (int o = 0; o < 6; ++o)
                     yv[o] = __shfl_sync(full_mask, v[o] + b5[o], src);
-                if (P < p.n) {
+                if (P < n_pts) {
                     const double au = 1.495978707e11;
-                    const float rm = (float)p.out.r_max;
-                    const float X0 = __ldg(p.x + 3 * P) * rm, X1 = __ldg(p.x + 3 * P + 1) * rm,
-                                X2 = __ldg(p.x + 3 * P + 2) * rm;
+                    const float ps = p.in.pos_scale;
+                    const float X0 = __ldg(p.in.p + 3 * P) * ps, X1 = __ldg(p.in.p + 3 * P + 1) * ps,
+                                X2 = __ldg(p.in.p + 3 * P + 2) * ps;
                     const float r2 = X0 * X0 + X1 * X1 + X2 * X2;
                     const float ir = rsqrtf(r2);
                     const float a = (float)au * ir;                   // AU / r
                     const float bs = (float)p.out.B_scale * a * a;    // B per unit y_B
                     const float es = (float)p.out.E_scale * a;        // E per unit y_E
-                    float *dst = p.out.field + P * 24;
+                    float *dst = p.out.field + P * p.out.field_stride;
                     if (q == 0) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
                         const int d = q - 1;
                         const float Xd = d == 0 ? X0 : (d == 1 ? X1 : X2);
-                        const float irm = 1.0f / rm;
+                        const float irm = p.in.x_scale / ps;  // d/dR = (x_scale / pos_scale) d/dx
                         const float ur = Xd * ir * ir;  // R_d / r^2
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -404,21 +408,20 @@ int siren_eval_grid(int64_t n)
     return (int)(tiles < n_sm ? tiles : n_sm);
 }
 
-cudaError_t siren_eval(const SirenNet &net, const float *x, int64_t n, const SirenOut &out, cudaStream_t s)
+cudaError_t siren_eval(const SirenNet &net, const SirenIn &in, const SirenOut &out, cudaStream_t s)
 {
-    if (n <= 0) return cudaSuccess;
+    if (in.n <= 0) return cudaSuccess;
     if (!net.err) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(siren_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     EvalParams p;
     p.P = net.P;
-    p.x = x;
-    p.n = n;
+    p.in = in;
     p.out = out;
     p.omega0 = net.omega0;
     p.err = net.err;
-    siren_eval_kernel<<<siren_eval_grid(n), kThreads, kSmemBytes, s>>>(net.map_wh, net.map_w5, p);
+    siren_eval_kernel<<<siren_eval_grid(in.n), kThreads, kSmemBytes, s>>>(net.map_wh, net.map_w5, p);
     return cudaGetLastError();
 }
 

@@ -125,7 +125,8 @@ class StatsOut(C.Structure):
                 ("particle_steps", C.c_uint64), ("collisions", C.c_uint64),
                 ("rebirths", C.c_uint64), ("flags_or", C.c_uint32), ("pad0", C.c_uint32),
                 ("kernel_launches", C.c_uint64), ("push_launches", C.c_uint64),
-                ("push_ms", C.c_double), ("sorts", C.c_uint64), ("sort_ms", C.c_double)]
+                ("push_ms", C.c_double), ("sorts", C.c_uint64), ("sort_ms", C.c_double),
+                ("field_evals", C.c_uint64), ("field_ms", C.c_double)]
 
 
 class SirenDesc(C.Structure):
@@ -140,7 +141,7 @@ class FitDesc(C.Structure):
 
 
 SIREN_NPARAMS = 200456
-FIELD_GRID, FIELD_SIREN = 0, 1
+FIELD_GRID, FIELD_SIREN, FIELD_GRID_SAMPLED = 0, 1, 2
 
 
 class LaunchChoice(C.Structure):

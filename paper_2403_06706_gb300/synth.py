@@ -249,3 +249,24 @@ def field_scales(w: WindSpec) -> dict:
     """Scaling of the network's inputs and outputs: x = R / r_max; outputs are
     B (r / 1 AU)^2 / B1, E (r / 1 AU) / (B1 u_sw), |B| (r / 1 AU)^2 / B1 and Phi / (B1 u_sw AU)."""
     return {"r_scale": w.r_max_au * AU, "B_scale": w.B1, "E_scale": w.B1 * w.u_sw}
+
+
+def siren_samples(n: int, w: WindSpec, seed: int = 0) -> np.ndarray:
+    """n training points uniform in the volume of the grid's shell r_min <= r <= r_max,
+    scaled by r_max (x = R / r_max), float32 (n, 3)."""
+    rng = np.random.default_rng(seed + 2000)
+    a, b = w.r_min_au**3, w.r_max_au**3
+    r = (a + rng.uniform(0.0, 1.0, n) * (b - a)) ** (1.0 / 3.0) / w.r_max_au
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return (v * r[:, None]).astype(np.float32)
+
+
+def c4_neural(n: int = 10_000_000) -> Workload:
+    """The perturbed Parker field of c2_perturbed replaced by a SIREN trained on 10^7
+    uniform-in-volume samples of its grid interpolant; n electrons at 81 keV, lambda 0.5 AU."""
+    w = WindSpec(256, 128, 256, eps=0.1, n_modes=8)
+    e = EnsembleSpec(n, lam_au=0.5, r_out_au=r_out_default(w))
+    return Workload("siren_parker256x128x256_eps0.1_8modes_1e7e", w, (e,), 0.5, 172800, "f32",
+                    extra={"n_samples": 10_000_000, "epochs": 10, "batch": 65536, "lr": 2e-4,
+                           "omega0": SIREN_OMEGA0})

@@ -165,3 +165,35 @@ def test_physical_field_is_the_derivative_of_the_unscaled_network():
         bm, em = BE(x * rs - e_)
         np.testing.assert_allclose(dB[:, d, :], (bp - bm) / (2 * h), rtol=1e-5, atol=1e-6 * np.abs(dB).max())
         np.testing.assert_allclose(dE[:, d, :], (ep - em) / (2 * h), rtol=1e-5, atol=1e-6 * np.abs(dE).max())
+
+
+def test_c_oracle_neural_field_matches_numpy_reading():
+    """The C oracle's neural field (used by its push) against the numpy reading above, in
+    both arithmetics, and its Jacobians against finite differences of its own values."""
+    import oracle
+    p = _small_params()
+    rs, Bs, Es = 2.5 * siren.AU, 3.5e-9, 1.4e-3
+    for bf16 in (False, True):
+        f = oracle.siren_field(p, W0, rs, Bs, Es, bf16=bf16)
+        x = RNG.uniform(-0.8, 0.8, (6, 3))
+        y, J = siren.forward(p, x, W0, jac=True, bf16=bf16)
+        B, E, dB, dE = siren.physical_field(x, y, J, rs, Bs, Es)
+        for q in range(6):
+            s, fl = oracle.field_eval(f, x[q] * rs)
+            assert fl == 0
+            np.testing.assert_allclose(s["B"], B[q], rtol=1e-10, atol=1e-12 * np.abs(B).max())
+            np.testing.assert_allclose(s["E"], E[q], rtol=1e-10, atol=1e-12 * np.abs(E).max())
+            # oracle JB[c][d] = dB_c / dR_d; physical_field dB[d][c]
+            np.testing.assert_allclose(s["JB"], dB[q].T, rtol=1e-9, atol=1e-12 * np.abs(dB).max())
+            np.testing.assert_allclose(s["JE"], dE[q].T, rtol=1e-9, atol=1e-12 * np.abs(dE).max())
+    f = oracle.siren_field(p, W0, rs, Bs, Es)
+    R = np.array([0.4, -0.3, 0.2]) * rs
+    s0, _ = oracle.field_eval(f, R)
+    h = 1e-6 * rs
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        sp, _ = oracle.field_eval(f, R + e)
+        sm, _ = oracle.field_eval(f, R - e)
+        np.testing.assert_allclose(s0["JB"][:, d], (sp["B"] - sm["B"]) / (2 * h), rtol=1e-5,
+                                   atol=1e-6 * np.abs(s0["JB"]).max())
