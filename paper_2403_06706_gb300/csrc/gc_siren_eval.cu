@@ -7,18 +7,24 @@
 //   layer k:  z = W_k h_{k-1} + b_k, h_k = sin z, t_{k,j} = cos(z) * (W_k t_{k-1,j})
 //   output:   y = W5 h4 + b5,       J[:, j] = W5 t_{4,j}.
 // A tile is 64 points = 256 rows (row 4p + q: q = 0 value, q = 1..3 tangents). Hidden
-// layers run as D = W_k . H^T on the tensor cores (M = 128 output features per half,
+// layers run as D = W_k . H^T on the tensor cores (two halves of M = 128 output features,
 // N = 256 rows, K = 256), so that each accumulator lane holds one feature and the four rows
 // of a point sit in adjacent columns: the epilogue thread of a feature computes sin and cos
 // of the value row once and scales its own three tangent columns, with no data exchange.
 // Activations go back to shared memory in the MN-major 128-byte-swizzled layout that the
 // next layer reads as its B operand. The output layer runs as rows x W5^T (M = 128 rows,
-// N = 16 with W5 zero-padded). Weights stream through a 3-stage TMA ring (32 KB chunks of
-// 64 input features x 256 outputs); the first layer runs on the CUDA cores.
+// N = 16 with W5 zero-padded). Weights stream through a 6-stage TMA ring (16 KB chunks of
+// 64 input features x 128 outputs); the first layer runs on the CUDA cores.
 //
-// Warp roles (320 threads): warps 0-7 compute (feature f = 128 (w / 4) + 32 (w % 4) + lane;
-// warp w may only touch tensor-memory lanes 32 (w % 4) .. + 31), warp 8 lane 0 issues the
-// MMAs (warp 8 also owns the tensor-memory allocation), warp 9 lane 0 issues the TMA loads.
+// Pipeline of one layer: the MMAs of output half 0 (all K), then half 1 in two K halves.
+// The epilogue of half 0 overlaps the MMAs of half 1 (it may overwrite input features
+// 0-127 once half 1 has consumed them), and the epilogue of half 1 overlaps the next
+// layer's half-0 MMAs over input features 0-127 (the features half 0 has just written).
+//
+// Warp roles (576 threads): warps 0-15 compute; warp w handles output half hh = (w / 4) % 2,
+// feature f = 128 hh + 32 (w % 4) + lane and rows 128 cg .. 128 cg + 127, cg = w / 8 (warp
+// w may only touch tensor-memory lanes 32 (w % 4) .. + 31). Warp 16 lane 0 issues the MMAs
+// (warp 16 also owns the tensor-memory allocation), warp 17 lane 0 issues the TMA loads.
 // Every wait is bounded: a wait that runs out sets the kernel's error word and an abort flag
 // that makes all roles leave their loops; the CTA then waits for its own copies and MMAs
 // and frees its tensor memory.
@@ -38,14 +44,15 @@ using namespace tc;
 namespace {
 
 constexpr int kPts = 64;                        // points per tile
-constexpr int kStagesW = 3;                     // weight ring depth
-constexpr uint32_t kChunkBytes = 256u * 128u;   // 256 rows x 64 bf16
+constexpr int kStagesW = 6;                     // weight ring depth
+constexpr uint32_t kChunkBytes = 128u * 128u;   // 128 output rows x 64 bf16
 constexpr uint32_t kW5Bytes = 4u * 16u * 128u;  // W5 padded: 4 boxes of 16 rows x 64 bf16
 constexpr uint32_t kHBytes = 32u * 4u * 1024u;  // 32 K-groups x 4 MN-blocks of 1024 B
-constexpr int kChunksPerTile = 3 * 4 + 1;
-constexpr int kComputeThreads = 256;
-constexpr int kThreads = 320;
-constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + 1024 + 128;
+constexpr int kChunksPerTile = 3 * 8 + 1;
+constexpr int kHalfThreads = 256;               // compute threads per output half
+constexpr int kThreads = 576;
+constexpr int kMmaWarp = 16, kTmaWarp = 17;
+constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + 1024 + 256;
 
 struct EvalParams {
     const float *P;  // master parameters
@@ -111,9 +118,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sW = smem + kHBytes;
     uint64_t *full = (uint64_t *)(sW + kStagesW * kChunkBytes);
     uint64_t *empty = full + kStagesW;
-    uint64_t *h_ready = empty + kStagesW;
-    uint64_t *acc_ready = h_ready + 1;
-    uint64_t *fin = acc_ready + 1;
+    uint64_t *h_ready = empty + kStagesW; // [2]: activations of a half written, its accumulator drained
+    uint64_t *acc = h_ready + 2;          // [2]: accumulator of a half complete
+    uint64_t *kdone = acc + 2;            // half 1 has consumed input features 0-127
+    uint64_t *acc_out = kdone + 1;        // output layer complete
+    uint64_t *fin = acc_out + 1;
     uint32_t *tmem_slot = (uint32_t *)(fin + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
@@ -130,13 +139,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(h_ready, kComputeThreads);
-        mbar_init(acc_ready, 1);
+        mbar_init(&h_ready[0], kHalfThreads);
+        mbar_init(&h_ready[1], kHalfThreads);
+        mbar_init(&acc[0], 1);
+        mbar_init(&acc[1], 1);
+        mbar_init(kdone, 1);
+        mbar_init(acc_out, 1);
         mbar_init(fin, 1);
         *abort = 0;
         mbar_fence_init();
     }
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
@@ -145,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 9) {
+    if (warp == kTmaWarp) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             uint32_t g = 0;
@@ -158,9 +171,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t *dst = sW + s * kChunkBytes;
-                    if (c < 12) {
+                    if (c < 24) {
+                        // chunk (layer c / 8, output half (c / 4) % 2, input block c % 4)
                         mbar_expect_tx(&full[s], kChunkBytes);
-                        tma_load_2d(dst, &mwh, (c & 3) * 64, (c >> 2) * 256, &full[s]);
+                        tma_load_2d(dst, &mwh, (c & 3) * 64, (c >> 3) * 256 + ((c >> 2) & 1) * 128, &full[s]);
                     } else {
                         mbar_expect_tx(&full[s], kW5Bytes);
                         for (int kb = 0; kb < 4; ++kb)
@@ -173,60 +187,66 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (uint32_t j = g > (uint32_t)kStagesW ? g - kStagesW : 0u; j < g; ++j)
                 mbar_wait(&full[j % kStagesW], (j / kStagesW) & 1u);
         }
-    } else if (warp == 8) {
+    } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t id_hid = idesc_bf16_f32(128, 256, 0, 1);
             const uint32_t id_out = idesc_bf16_f32(128, 16, 1, 0);
             const uint32_t hb = smem_u32(sH);
-            uint32_t g = 0, nh = 0;
+            uint32_t g = 0, nh0 = 0, nh1 = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 for (int L = 0; L < 3 && ok; ++L) {
-                    if (!wait_abort(h_ready, nh & 1u, abort, p.err, 12)) {
-                        ok = false;
-                        break;
-                    }
-                    ++nh;
-                    tc_fence_after();
-                    for (int kb = 0; kb < 4; ++kb) {
-                        const uint32_t s = g % kStagesW;
-                        if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 13)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t wb = smem_u32(sW + s * kChunkBytes);
-#pragma unroll
-                        for (int h = 0; h < 2; ++h)
+                    for (int h = 0; h < 2 && ok; ++h) {
+                        for (int kb = 0; kb < 4; ++kb) {
+                            if (h == 0 && kb == 0) {
+                                // inputs 0-127 written and accumulator half 0 drained
+                                if (!wait_abort(&h_ready[0], nh0 & 1u, abort, p.err, 12)) { ok = false; break; }
+                                ++nh0;
+                                tc_fence_after();
+                            }
+                            if (h == 0 && kb == 2) {
+                                // inputs 128-255 written and accumulator half 1 drained
+                                if (!wait_abort(&h_ready[1], nh1 & 1u, abort, p.err, 13)) { ok = false; break; }
+                                ++nh1;
+                                tc_fence_after();
+                            }
+                            const uint32_t s = g % kStagesW;
+                            if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 14)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t wb = smem_u32(sW + s * kChunkBytes);
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks)
-                                mma_bf16(tmem + h * 256, desc_sw128(wb + h * 16384 + ks * 32),
+                                mma_bf16(tmem + h * 256, desc_sw128(wb + ks * 32),
                                          desc_sw128_mn(hb + (kb * 4 + ks) * 8192, 1024, 4096), id_hid,
                                          (kb | ks) ? 1u : 0u);
-                        mma_commit(&empty[s]);
-                        ++g;
+                            mma_commit(&empty[s]);
+                            ++g;
+                            if (h == 1 && kb == 1) mma_commit(kdone);
+                        }
+                        if (ok) mma_commit(&acc[h]);
                     }
-                    if (ok) mma_commit(acc_ready);
                 }
                 if (!ok) break;
-                // output layer: rows x W5^T, two M-tiles of 128 rows into columns 0-15, 16-31
-                if (!wait_abort(h_ready, nh & 1u, abort, p.err, 14)) break;
-                ++nh;
+                // output layer: rows x W5^T; M-tile 0 into columns 0-15, M-tile 1 into 256-271
+                if (!wait_abort(&h_ready[0], nh0 & 1u, abort, p.err, 15)) break;
+                ++nh0;
+                if (!wait_abort(&h_ready[1], nh1 & 1u, abort, p.err, 16)) break;
+                ++nh1;
                 tc_fence_after();
                 const uint32_t s = g % kStagesW;
-                if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 15)) break;
+                if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 17)) break;
                 tc_fence_after();
                 const uint32_t wb = smem_u32(sW + s * kChunkBytes);
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                     for (int k16 = 0; k16 < 16; ++k16)
-                        mma_bf16(tmem + mt * 16, desc_sw128_mn(hb + mt * 2048 + k16 * 8192, 1024, 4096),
+                        mma_bf16(tmem + mt * 256, desc_sw128_mn(hb + mt * 2048 + k16 * 8192, 1024, 4096),
                                  desc_sw128(wb + (k16 >> 2) * 2048 + (k16 & 3) * 32), id_out, k16 ? 1u : 0u);
                 mma_commit(&empty[s]);
                 ++g;
-                mma_commit(acc_ready);
+                mma_commit(acc_out);
             }
             // all MMAs of this CTA complete before its tensor memory is released
             mma_commit(fin);
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------------------ compute warps
-        const int lq = warp & 3, hh = warp >> 2;
+        const int lq = warp & 3, hh = (warp >> 2) & 1, cg = warp >> 3;
         const int f = hh * 128 + lq * 32 + lane;
         const float w0 = p.omega0;
         const float w1x = p.P[siren_oW(1) + 3 * f], w1y = p.P[siren_oW(1) + 3 * f + 1],
@@ -250,24 +270,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16);
         uint8_t *hrow = sH + (f >> 3) * 4096 + (f & 7) * 128;
         const uint32_t rsw = (uint32_t)(f & 7);
-        uint32_t na = 0;
+        uint32_t na = 0, nk = 0, no = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int64_t base = t * kPts;
-            // layer 1 on the CUDA cores
-#pragma unroll 1
-            for (int p2 = 0; p2 < kPts / 2; ++p2) {
+            // layer 1 on the CUDA cores: this thread's feature for points 32 cg .. 32 cg + 31
+#pragma unroll 2
+            for (int p2 = 0; p2 < 16; ++p2) {
+                const int pl = cg * 32 + 2 * p2;
+                float xv[6];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int64_t P = base + pl + e;
+                    const bool in = P < n_pts;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        xv[3 * e + j] = in ? __ldg(p.in.p + 3 * P + j) * p.in.x_scale : 0.f;
+                }
                 float o[8];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const int64_t P = base + 2 * p2 + e;
-                    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-                    if (P < n_pts) {
-                        x0 = __ldg(p.in.p + 3 * P) * p.in.x_scale;
-                        x1 = __ldg(p.in.p + 3 * P + 1) * p.in.x_scale;
-                        x2 = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
-                    }
-                    const float z = w0 * fmaf(w1x, x0, fmaf(w1y, x1, fmaf(w1z, x2, b1)));
+                    const float z = w0 * fmaf(w1x, xv[3 * e], fmaf(w1y, xv[3 * e + 1], fmaf(w1z, xv[3 * e + 2], b1)));
                     float sn, cs;
                     sincos_rr(z, sn, cs);
                     const float wc = w0 * cs;
@@ -276,51 +299,64 @@ __global__ void __launch_bounds__(kThreads, 1)
                     o[4 * e + 2] = wc * w1y;
                     o[4 * e + 3] = wc * w1z;
                 }
-                store_rows8(hrow, rsw, 8u * p2, o);
+                store_rows8(hrow, rsw, 4u * (uint32_t)pl, o);
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(h_ready);
-            // hidden layers 2-4: epilogue of D = W_k H^T
+            mbar_arrive(&h_ready[hh]);
+            // hidden layers 2-4: epilogue of this half's D = W_k H^T
             for (int L = 0; L < 3; ++L) {
-                if (!wait_abort(acc_ready, na & 1u, abort, p.err, 16)) {
+                if (!wait_abort(&acc[hh], na & 1u, abort, p.err, 18)) {
                     ok = false;
                     break;
                 }
                 ++na;
                 tc_fence_after();
                 const float b = bl[L];
+                bool may_store = (hh == 1);
 #pragma unroll 1
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < 4; ++c) {
                     float v[32];
-                    tmem_ld32(lane_base + hh * 256 + c * 32, v);
+                    tmem_ld32(lane_base + hh * 256 + cg * 128 + c * 32, v);
+                    float o[4][8];
 #pragma unroll
-                    for (int pp = 0; pp < 4; ++pp) {
-                        float o[8];
+                    for (int pp = 0; pp < 4; ++pp)
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             const int q0 = 8 * pp + 4 * e;
                             float sn, cs;
                             sincos_rr(v[q0] + b, sn, cs);
-                            o[4 * e] = sn;
-                            o[4 * e + 1] = cs * v[q0 + 1];
-                            o[4 * e + 2] = cs * v[q0 + 2];
-                            o[4 * e + 3] = cs * v[q0 + 3];
+                            o[pp][4 * e] = sn;
+                            o[pp][4 * e + 1] = cs * v[q0 + 1];
+                            o[pp][4 * e + 2] = cs * v[q0 + 2];
+                            o[pp][4 * e + 3] = cs * v[q0 + 3];
                         }
-                        store_rows8(hrow, rsw, (uint32_t)(c * 32 + 8 * pp), o);
+                    if (!may_store) {
+                        // half 1 still reads input features 0-127 until kdone
+                        if (!wait_abort(kdone, nk & 1u, abort, p.err, 19)) {
+                            ok = false;
+                            break;
+                        }
+                        may_store = true;
                     }
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp)
+                        store_rows8(hrow, rsw, (uint32_t)(cg * 128 + c * 32 + 8 * pp), o[pp]);
                 }
+                if (hh == 0) ++nk;
+                if (!ok) break;
                 fence_proxy_async_smem();
                 tc_fence_before();
-                mbar_arrive(h_ready);
+                mbar_arrive(&h_ready[hh]);
             }
             if (!ok) break;
-            // output layer
-            if (!wait_abort(acc_ready, na & 1u, abort, p.err, 17)) break;
-            ++na;
+            // output layer (all compute warps wait: the next tile's layer 1 overwrites H4)
+            if (!wait_abort(acc_out, no & 1u, abort, p.err, 20)) break;
+            ++no;
             tc_fence_after();
+            if (cg != 0) continue;
             float v[16];
-            tmem_ld16(lane_base + hh * 16, v);
+            tmem_ld16(lane_base + hh * 256, v);
             tc_fence_before();
             const int pr = hh * 128 + lq * 32 + lane;
             const int q = pr & 3;
@@ -380,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
@@ -390,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 cudaError_t siren_maps(SirenNet &net)
 {
-    cudaError_t e = make_map_bf16(&net.map_wh, net.Wh, 256, 3 * 256, 256);
+    cudaError_t e = make_map_bf16(&net.map_wh, net.Wh, 256, 3 * 256, 128);
     if (e == cudaSuccess) e = make_map_bf16(&net.map_w5, net.W5p, 256, 16, 16);
     return e;
 }
