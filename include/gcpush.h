@@ -230,9 +230,9 @@ int gc_version(void);
 
 /* BF16 tensor-core GEMM used by the neural-field training: C = A B^T with A (M x K) and
  * B (N x K) bf16 row-major on the device (K contiguous, 16-byte aligned), FP32 accumulate,
- * C (M x N) FP32 row-major on the device. accumulate != 0 adds into C with atomics, which
- * split_k > 1 requires (K is then split over split_k CTAs per tile). M and N must be
- * multiples of 128 and K of 64. Runs on stream and synchronises it. */
+ * C (M x N) FP32 row-major on the device (16-byte aligned). accumulate != 0 adds into C
+ * with atomics, which split_k > 1 requires (K is then split over split_k CTAs per tile).
+ * M and N must be multiples of 128 and K of 64. Runs on stream and synchronises it. */
 int gc_gemm_bf16_tn(const void *A, const void *B, float *C, int M, int N, int K, int split_k, int accumulate,
                     void *stream);
 

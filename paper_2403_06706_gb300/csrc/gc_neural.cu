@@ -355,7 +355,7 @@ cudaError_t fwd_bwd(Neural &nn, const float *x, const float *t, int64_t n, float
                                                     nn.dZ, grad, nn.d_loss);
     // K = n split so that about two waves of CTAs share each dW product
     const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(n / 64, 152));
-    const int rows_per_block = 256;
+    const int rows_per_block = 32;
     const int bb = (int)((n + rows_per_block - 1) / rows_per_block);
     for (int L = 4; L >= 2; --L) {
         e = gcs::gemm_bf16(nn.dZ, 1, H[L - 2], 1, grad + siren_oW(L), 256, 256, (int)n, splits, 1, s);

@@ -155,15 +155,16 @@ __global__ void __launch_bounds__(128, 1)
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (row < M && s_ok) {
-                float *dst = C + (size_t)row * ldc + n0 + c0;
+                // N is a multiple of the tile width and ldc of 4: whole float4 chunks
+                float4 *dst = reinterpret_cast<float4 *>(C + (size_t)row * ldc + n0 + c0);
                 if (atomic) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (n0 + c0 + j < N) atomicAdd(dst + j, v[j]);
+                    for (int j = 0; j < 8; ++j)
+                        atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (n0 + c0 + j < N) dst[j] = v[j];
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
             }
         }
@@ -279,8 +280,8 @@ extern "C" int gc_gemm_bf16(const void *A, int a_mn, const void *B, int b_mn, fl
         gcp::set_last_error("gc_gemm_bf16: need M % 128 == 0, N % 128 == 0, K % 64 == 0");
         return GC_ERR_INVALID;
     }
-    if (((uintptr_t)A | (uintptr_t)B) & 15) {
-        gcp::set_last_error("gc_gemm_bf16: A and B must be 16-byte aligned");
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15) {
+        gcp::set_last_error("gc_gemm_bf16: A, B and C must be 16-byte aligned");
         return GC_ERR_INVALID;
     }
     if (split_k > 1 && !accumulate) {

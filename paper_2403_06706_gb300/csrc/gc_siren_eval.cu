@@ -21,9 +21,9 @@
 // 0-127 once half 1 has consumed them), and the epilogue of half 1 overlaps the next
 // layer's half-0 MMAs over input features 0-127 (the features half 0 has just written).
 //
-// Warp roles (576 threads): warps 0-15 compute; warp w handles output half hh = (w / 4) % 2,
-// feature f = 128 hh + 32 (w % 4) + lane and rows 128 cg .. 128 cg + 127, cg = w / 8 (warp
-// w may only touch tensor-memory lanes 32 (w % 4) .. + 31). Warp 16 lane 0 issues the MMAs
+// Warp roles (576 threads): warps 0-15 compute; all of them work on one output half at a
+// time, warp w on features 32 (w % 4) + lane of the half (warp w may only touch
+// tensor-memory lanes 32 (w % 4) .. + 31) and rows 64 (w / 4) .. + 63. Warp 16 lane 0 issues the MMAs
 // (warp 16 also owns the tensor-memory allocation), warp 17 lane 0 issues the TMA loads.
 // Every wait is bounded: a wait that runs out sets the kernel's error word and an abort flag
 // that makes all roles leave their loops; the CTA then waits for its own copies and MMAs
@@ -49,7 +49,7 @@ constexpr uint32_t kChunkBytes = 128u * 128u;   // 128 output rows x 64 bf16
 constexpr uint32_t kW5Bytes = 4u * 16u * 128u;  // W5 padded: 4 boxes of 16 rows x 64 bf16
 constexpr uint32_t kHBytes = 32u * 4u * 1024u;  // 32 K-groups x 4 MN-blocks of 1024 B
 constexpr int kChunksPerTile = 3 * 8 + 1;
-constexpr int kHalfThreads = 256;               // compute threads per output half
+constexpr int kComputeThreads = 512;            // arrivals on each h_ready barrier
 constexpr int kThreads = 576;
 constexpr int kMmaWarp = 16, kTmaWarp = 17;
 constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + 1024 + 256;
@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&h_ready[0], kHalfThreads);
-        mbar_init(&h_ready[1], kHalfThreads);
+        mbar_init(&h_ready[0], kComputeThreads);
+        mbar_init(&h_ready[1], kComputeThreads);
         mbar_init(&acc[0], 1);
         mbar_init(&acc[1], 1);
         mbar_init(kdone, 1);
@@ -254,111 +254,134 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------------------ compute warps
-        const int lq = warp & 3, hh = (warp >> 2) & 1, cg = warp >> 3;
-        const int f = hh * 128 + lq * 32 + lane;
+        // warp w: tensor-memory lane quarter lq = w % 4 (features 32 lq .. of each half) and
+        // row group rg = w / 4 (rows 64 rg .. 64 rg + 63 = points 16 rg .. 16 rg + 15); all
+        // 16 warps work on one output half at a time
+        const int lq = warp & 3, rg = warp >> 2;
         const float w0 = p.omega0;
-        const float w1x = p.P[siren_oW(1) + 3 * f], w1y = p.P[siren_oW(1) + 3 * f + 1],
-                    w1z = p.P[siren_oW(1) + 3 * f + 2], b1 = p.P[siren_oB(1) + f];
-        float bl[3];
+        float w1[2][3], b1[2], bl[3][2];
 #pragma unroll
-        for (int L = 0; L < 3; ++L)
-            bl[L] = p.P[siren_oB(L + 2) + f];
+        for (int h = 0; h < 2; ++h) {
+            const int f = h * 128 + lq * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                w1[h][j] = p.P[siren_oW(1) + 3 * f + j];
+            b1[h] = p.P[siren_oB(1) + f];
+#pragma unroll
+            for (int L = 0; L < 3; ++L)
+                bl[L][h] = p.P[siren_oB(L + 2) + f];
+        }
         float b5[8];
 #pragma unroll
         for (int o = 0; o < 8; ++o)
             b5[o] = p.P[siren_oB(5) + o];
         const uint32_t lane_base = tmem + ((uint32_t)(lq * 32) << 16);
-        uint8_t *hrow = sH + (f >> 3) * 4096 + (f & 7) * 128;
-        const uint32_t rsw = (uint32_t)(f & 7);
-        uint32_t na = 0, nk = 0, no = 0;
+        // the feature's 128-byte row in its K-group's first atom, for each half
+        uint8_t *hrow0 = sH + ((lq * 32 + lane) >> 3) * 4096 + (lane & 7) * 128;
+        uint8_t *hrow1 = hrow0 + 16 * 4096;
+        const uint32_t rsw = (uint32_t)(lane & 7);
+        const unsigned full_mask = 0xffffffffu;
+        uint32_t na0 = 0, na1 = 0, nk = 0, no = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int64_t base = t * kPts;
-            // layer 1 on the CUDA cores: this thread's feature for points 32 cg .. 32 cg + 31
-#pragma unroll 2
-            for (int p2 = 0; p2 < 16; ++p2) {
-                const int pl = cg * 32 + 2 * p2;
-                float xv[6];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int64_t P = base + pl + e;
-                    const bool in = P < n_pts;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        xv[3 * e + j] = in ? __ldg(p.in.p + 3 * P + j) * p.in.x_scale : 0.f;
+            // this warp's 16 points: lane i < 16 holds point 16 rg + i, shared by shuffles
+            float px = 0.f, py = 0.f, pz = 0.f;
+            {
+                const int64_t P = base + rg * 16 + (lane & 15);
+                if (P < n_pts) {
+                    px = __ldg(p.in.p + 3 * P) * p.in.x_scale;
+                    py = __ldg(p.in.p + 3 * P + 1) * p.in.x_scale;
+                    pz = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
                 }
-                float o[8];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const float z = w0 * fmaf(w1x, xv[3 * e], fmaf(w1y, xv[3 * e + 1], fmaf(w1z, xv[3 * e + 2], b1)));
-                    float sn, cs;
-                    sincos_rr(z, sn, cs);
-                    const float wc = w0 * cs;
-                    o[4 * e] = sn;
-                    o[4 * e + 1] = wc * w1x;
-                    o[4 * e + 2] = wc * w1y;
-                    o[4 * e + 3] = wc * w1z;
-                }
-                store_rows8(hrow, rsw, 4u * (uint32_t)pl, o);
             }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            mbar_arrive(&h_ready[hh]);
-            // hidden layers 2-4: epilogue of this half's D = W_k H^T
-            for (int L = 0; L < 3; ++L) {
-                if (!wait_abort(&acc[hh], na & 1u, abort, p.err, 18)) {
-                    ok = false;
-                    break;
-                }
-                ++na;
-                tc_fence_after();
-                const float b = bl[L];
-                bool may_store = (hh == 1);
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    float v[32];
-                    tmem_ld32(lane_base + hh * 256 + cg * 128 + c * 32, v);
-                    float o[4][8];
+            // layer 1 on the CUDA cores, half 0 then half 1
 #pragma unroll
-                    for (int pp = 0; pp < 4; ++pp)
+            for (int h = 0; h < 2; ++h) {
+                uint8_t *hrow = h ? hrow1 : hrow0;
+#pragma unroll 2
+                for (int p2 = 0; p2 < 8; ++p2) {
+                    float o[8];
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int q0 = 8 * pp + 4 * e;
-                            float sn, cs;
-                            sincos_rr(v[q0] + b, sn, cs);
-                            o[pp][4 * e] = sn;
-                            o[pp][4 * e + 1] = cs * v[q0 + 1];
-                            o[pp][4 * e + 2] = cs * v[q0 + 2];
-                            o[pp][4 * e + 3] = cs * v[q0 + 3];
-                        }
-                    if (!may_store) {
-                        // half 1 still reads input features 0-127 until kdone
-                        if (!wait_abort(kdone, nk & 1u, abort, p.err, 19)) {
-                            ok = false;
-                            break;
-                        }
-                        may_store = true;
+                    for (int e = 0; e < 2; ++e) {
+                        const int src = 2 * p2 + e;
+                        const float x0 = __shfl_sync(full_mask, px, src), x1 = __shfl_sync(full_mask, py, src),
+                                    x2 = __shfl_sync(full_mask, pz, src);
+                        const float z = w0 * fmaf(w1[h][0], x0, fmaf(w1[h][1], x1, fmaf(w1[h][2], x2, b1[h])));
+                        float sn, cs;
+                        sincos_rr(z, sn, cs);
+                        const float wc = w0 * cs;
+                        o[4 * e] = sn;
+                        o[4 * e + 1] = wc * w1[h][0];
+                        o[4 * e + 2] = wc * w1[h][1];
+                        o[4 * e + 3] = wc * w1[h][2];
                     }
-#pragma unroll
-                    for (int pp = 0; pp < 4; ++pp)
-                        store_rows8(hrow, rsw, (uint32_t)(cg * 128 + c * 32 + 8 * pp), o[pp]);
+                    store_rows8(hrow, rsw, (uint32_t)(rg * 64 + 8 * p2), o);
                 }
-                if (hh == 0) ++nk;
-                if (!ok) break;
                 fence_proxy_async_smem();
                 tc_fence_before();
-                mbar_arrive(&h_ready[hh]);
+                mbar_arrive(&h_ready[h]);
+            }
+            // hidden layers 2-4: epilogues of D = W_k H^T, half 0 then half 1
+            for (int L = 0; L < 3 && ok; ++L) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t &na = h ? na1 : na0;
+                    if (!wait_abort(&acc[h], na & 1u, abort, p.err, 18)) {
+                        ok = false;
+                        break;
+                    }
+                    ++na;
+                    tc_fence_after();
+                    uint8_t *hrow = h ? hrow1 : hrow0;
+                    const float b = bl[L][h];
+#pragma unroll 1
+                    for (int c = 0; c < 2; ++c) {
+                        float v[32];
+                        tmem_ld32(lane_base + h * 256 + rg * 64 + c * 32, v);
+                        float o[4][8];
+#pragma unroll
+                        for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                // |z| stays small in the hidden layers: the hardware sine
+                                // and cosine without a range reduction
+                                const int q0 = 8 * pp + 4 * e;
+                                const float z = v[q0] + b;
+                                const float sn = __sinf(z), cs = __cosf(z);
+                                o[pp][4 * e] = sn;
+                                o[pp][4 * e + 1] = cs * v[q0 + 1];
+                                o[pp][4 * e + 2] = cs * v[q0 + 2];
+                                o[pp][4 * e + 3] = cs * v[q0 + 3];
+                            }
+                        if (h == 0 && c == 0) {
+                            // half 1 reads input features 0-127 until kdone
+                            if (!wait_abort(kdone, nk & 1u, abort, p.err, 19)) {
+                                ok = false;
+                                break;
+                            }
+                            ++nk;
+                        }
+#pragma unroll
+                        for (int pp = 0; pp < 4; ++pp)
+                            store_rows8(hrow, rsw, (uint32_t)(rg * 64 + c * 32 + 8 * pp), o[pp]);
+                    }
+                    if (!ok) break;
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(&h_ready[h]);
+                }
             }
             if (!ok) break;
             // output layer (all compute warps wait: the next tile's layer 1 overwrites H4)
             if (!wait_abort(acc_out, no & 1u, abort, p.err, 20)) break;
             ++no;
             tc_fence_after();
-            if (cg != 0) continue;
+            if (rg >= 2) continue;
             float v[16];
-            tmem_ld16(lane_base + hh * 256, v);
+            tmem_ld16(lane_base + rg * 256, v);
             tc_fence_before();
-            const int pr = hh * 128 + lq * 32 + lane;
+            const int pr = rg * 128 + lq * 32 + lane;
             const int q = pr & 3;
             const int64_t P = base + (pr >> 2);
             if (p.out.field == nullptr) {

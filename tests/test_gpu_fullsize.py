@@ -65,3 +65,99 @@ def test_full_size_fp32_sampled_parity():
     eR = np.linalg.norm(R - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
     assert np.percentile(eR, 99) < 1e-5, np.percentile(eR, [50, 90, 99])
     np.testing.assert_array_equal(gs["flags"], st["flags"])
+
+
+def _oracle_subset(f, p, wl, n_s, first):
+    oe = oracle_ensembles(wl.ensembles)
+    parts = []
+    for k, f0 in enumerate(first):
+        counts = [0] * len(oe)
+        counts[k] = n_s
+        parts.append(oracle.inject(f, p, oe, counts, id0=int(f0), dt=wl.dt))
+    st = oracle.StateArrays({k: np.concatenate([q[k] for q in parts], axis=-1) for k in parts[0].arrays})
+    return oe, st
+
+
+def test_large_grid_fp32_sampled_parity_and_tally_invariants():
+    """The large workload: 512x256x512 FP32 grid (2.15 GB, eps = 0.2, 16 modes), 3x10^7
+    electrons with an E^-3 spectrum on [20, 500] keV, lambda = 0.3 AU, tallies of
+    pitch x energy x r on 64 x 64 x 128 bins; 1000 steps in the benchmark's launch shape.
+    The oracle recomputes the first 256 ids; the full tally is checked by its invariants:
+    every particle is sampled at every cadence step, and every in-range sample lands in
+    exactly one bin."""
+    import bench
+
+    wl = synth.c5_large()
+    nodes = synth.wind_grid(wl.wind, dtype=np.float32)
+    n_steps, cadence = 1000, 100
+    with gcpush.Context(precision=gcpush.PREC_FP32_MIXED, seed=wl.seed, dt_init=wl.dt) as c:
+        c.field_load(nodes, wl.wind.r_min_au, wl.wind.r_max_au)
+        c.inject(list(wl.ensembles))
+        c.set_launch(**bench.LAUNCH)
+        c.tally_arm(cadence=cadence, n_mu=64, n_E=64, n_r=128, E_lo_keV=5.0, E_hi_keV=600.0,
+                    r_lo_au=wl.wind.r_min_au, r_hi_au=wl.wind.r_max_au)
+        c.advance(wl.dt, n_steps)
+        g = c.get_state()
+        t = c.tally_read()
+    n = wl.n_particles
+    assert int(t["n_seen"][0]) == n * (n_steps // cadence)
+    assert int(t["h_mer"].sum(dtype=np.int64)) == int(t["n_seen"][0]) - int(t["n_seen"][1])
+    assert int(t["n_seen"][1]) < 0.01 * int(t["n_seen"][0])
+    n_s = 256
+    gs = {k: (v[:, :n_s] if v.ndim == 2 else v[:n_s]) for k, v in g.items()}
+    f = oracle.grid_field(nodes, wl.wind.r_min_au * AU, wl.wind.r_max_au * AU)
+    p = oracle.params(seed=wl.seed)
+    oe, st = _oracle_subset(f, p, wl, n_s, [0])
+    oracle.advance(f, p, oe, st, 0.0, 0, wl.dt, n_steps)
+    div = (gs["ncoll"] != st["ncoll"]) | (gs["event"] != st["event"]) | (gs["t_birth"] != st["t_birth"])
+    assert div.mean() <= 0.02, div.sum()
+    lam = np.full(n_s, wl.ensembles[0].lam_au * AU)
+    err = compare_states(gs, st.arrays, 1e-4, momentum_scale(st, nodes, wl.wind, wl.ensembles),
+                         skip=div, lam=lam)
+    for k, v in err.items():
+        assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+
+
+def test_neural_workload_sampled_parity():
+    """The neural-field workload: a SIREN trained on 10^7 samples of the perturbed
+    256x128x256 grid, then 10^7 electrons pushed with it for 20 steps. The oracle runs the
+    same network (BF16 reading) for the first 256 ids; increments of R and gamma v_par are
+    compared against their own size (the network's BF16 noise bounds the agreement,
+    tests/test_gpu_split.py)."""
+    wn = synth.c4_neural()
+    X = wn.extra
+    w = wn.wind
+    nodes = synth.wind_grid(w, dtype=np.float32)
+    n_steps = 20
+    with gcpush.Context(precision=gcpush.PREC_FP32_MIXED, seed=wn.seed, dt_init=wn.dt) as c:
+        c.field_load(nodes, w.r_min_au, w.r_max_au)
+        c.siren_set(synth.siren_init(seed=0), omega0=X["omega0"], r_max_au=w.r_max_au, B_scale=w.B1,
+                    E_scale=w.B1 * w.u_sw)
+        c.field_fit(synth.siren_samples(X["n_samples"], w), n_epochs=X["epochs"], batch=X["batch"], lr=X["lr"])
+        P = c.siren_get()
+        c.field_select(gcpush.FIELD_SIREN)
+        c.inject(list(wn.ensembles))
+        g0 = c.get_state()
+        c.advance(wn.dt, n_steps)
+        g1 = c.get_state()
+    n_s = 256
+    sl = lambda a: {k: (v[:, :n_s] if v.ndim == 2 else v[:n_s]) for k, v in a.items()}  # noqa: E731
+    g0, g1 = sl(g0), sl(g1)
+    f = oracle.siren_field(P, X["omega0"], w.r_max_au * AU, w.B1, w.B1 * w.u_sw, bf16=True)
+    p = oracle.params(seed=wn.seed)
+    oe, o0 = _oracle_subset(f, p, wn, n_s, [0])
+    np.testing.assert_array_equal(g0["u"], o0["u"])
+    o1 = o0.copy()
+    oracle.advance(f, p, oe, o1, 0.0, 0, wn.dt, n_steps)
+    same = (g1["ncoll"] == o1["ncoll"]) & (g1["t_birth"] == o1["t_birth"])
+    assert same.mean() > 0.97
+    R0 = np.stack([o0["x"], o0["y"], o0["z"]])
+    dRg = np.stack([g1["x"], g1["y"], g1["z"]]) - R0
+    dRo = np.stack([o1["x"], o1["y"], o1["z"]]) - R0
+    eR = np.linalg.norm(dRg - dRo, axis=0)[same] / np.linalg.norm(dRo, axis=0)[same]
+    du_scale = np.abs(o1["u"] - o0["u"])[same] + 1e-3 * np.abs(o0["u"])[same]
+    eu = np.abs((g1["u"] - g0["u"]) - (o1["u"] - o0["u"]))[same] / du_scale
+    print("increments: R rms", np.sqrt(np.mean(eR**2)), "max", eR.max(), "| u rms", np.sqrt(np.mean(eu**2)),
+          "max", eu.max())
+    assert np.sqrt(np.mean(eR**2)) < 2e-3 and eR.max() < 3e-2
+    assert np.sqrt(np.mean(eu**2)) < 2e-2 and eu.max() < 0.2

@@ -228,3 +228,21 @@ def test_device_anomaly_is_reported_not_trapped(nodes64):
         st = c.get_state()
         assert st["flags"][3] & 4 and st["flags"][5] & 1
         assert np.all(st["flags"][[0, 1, 2, 4, 6, 7]] == 0)
+
+
+def test_plain_fp64_workload_in_full():
+    """The plain FP64 workload as specified: 4096 electrons at 81 keV from r = 0.28 AU,
+    24 deg, lon 0, mu0 ~ U(0, 1], 64x32x64 FP64 Parker grid, lambda = 0.5 AU, dt = 0.5 s,
+    3600 steps (30 min), seed 0 - every particle against the oracle at 1e-9."""
+    wl = synth.c1_plain_fp64()
+    nodes = synth.wind_grid(wl.wind, dtype=np.float64)
+    calls = [(wl.dt, wl.n_steps, 0.0)]
+    ens = list(wl.ensembles)
+    g, _, gs = run_gpu(nodes, wl.wind, ens, calls, gcpush.PREC_FP64, seed=wl.seed)
+    o, _, os_ = run_oracle(nodes, wl.wind, ens, calls, seed=wl.seed)
+    _ints_equal(g, o)
+    np.testing.assert_array_equal(g["t_birth"], o["t_birth"])
+    assert gs["collisions"] == os_[0] > 1000
+    err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes, wl.wind, ens))
+    for k, v in err.items():
+        assert v < 1e-9, (k, v, err)
