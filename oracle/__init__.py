@@ -80,6 +80,7 @@ class Params(C.Structure):
         ("q", C.c_double), ("m", C.c_double), ("seed", C.c_uint32),
         ("collision_form", C.c_int32), ("drift_mask", C.c_int32),
         ("no_scatter", C.c_int32), ("no_rebirth", C.c_int32), ("pad0", C.c_int32),
+        ("wind_u", C.c_double),
     ]
 
 
@@ -231,11 +232,14 @@ def siren_field(params_flat, omega0: float, r_scale: float, B_scale: float, E_sc
 
 
 def params(seed: int = 0, q: float = Q_E, m: float = M_E, collision_form: int = 0,
-           drift_mask: int = 0, no_scatter: bool = False, no_rebirth: bool = False) -> Params:
+           drift_mask: int = 0, no_scatter: bool = False, no_rebirth: bool = False,
+           wind_u: float = 0.0) -> Params:
+    """wind_u > 0: collisions in the frame of a radial wind of that speed (m/s), Sect. 3.2."""
     p = Params()
     p.q, p.m, p.seed = q, m, seed
     p.collision_form, p.drift_mask = collision_form, drift_mask
     p.no_scatter, p.no_rebirth = int(no_scatter), int(no_rebirth)
+    p.wind_u = wind_u
     return p
 
 

@@ -94,6 +94,8 @@ typedef struct {
     int32_t no_scatter;     /* 1: never collide */
     int32_t no_rebirth;     /* 1: never reborn */
     int32_t pad0;
+    double wind_u;          /* > 0: collisions in the frame of a radial wind of this speed
+                               (m/s), Sect. 3.2; 0: in the fixed frame */
 } orc_params;
 
 typedef struct {
@@ -452,6 +454,7 @@ static void field_eval(const orc_field *f, const double R[3], orc_fields *o)
 
 typedef struct {
     double gamma, vpar, Bmag, Epar;
+    double b[3]; /* unit vector along B */
 } orc_aux;
 
 static void cross(const double a[3], const double b[3], double c[3])
@@ -542,6 +545,8 @@ static void rhs_from_fields(const orc_field *f, const orc_params *p, const orc_f
         aux->vpar = vpar;
         aux->Bmag = Bm;
         aux->Epar = Epar;
+        for (int i = 0; i < 3; ++i)
+            aux->b[i] = b[i];
     }
 }
 
@@ -834,12 +839,31 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
                     mu_new = 1.0 - 2.0 * a; /* Eq. 10 */
                 else
                     mu_new = ((w[0] & 1u) ? -1.0 : 1.0) * sqrt(a); /* Eq. 12 */
-                /* inertial-frame elastic collision: |p| fixed, B at R^{n+1} */
                 const double Bm = aux1.Bmag;
-                const double pm2 = X[3] * X[3] + 2.0 * mub * Bm / p->m; /* (|p|/m)^2 */
-                const double pm = sqrt(pm2);
-                X[3] = mu_new * pm;
-                mub = (1.0 - mu_new * mu_new) * pm2 * p->m / (2.0 * Bm);
+                if (p->wind_u > 0.0) {
+                    /* Sect. 3.2: elastic in the frame of the scattering centres, which
+                     * move with the wind u = wind_u R/r. The guiding centre already
+                     * drifts with the perpendicular part of u (the E x B drift), so
+                     * the frame change is a boost along b by V = u.b; p_perp is
+                     * unchanged by it. Per unit mass: u~ = g_V (u - V gamma),
+                     * gamma~ = g_V (gamma - V u / c^2), and back with -V. */
+                    const double V = p->wind_u * dot(X, aux1.b) / r1;
+                    const double gV = 1.0 / sqrt(1.0 - V * V / c2);
+                    const double pp2 = 2.0 * mub * Bm / p->m; /* (p_perp/m)^2 */
+                    const double gam = sqrt(1.0 + (X[3] * X[3] + pp2) / c2);
+                    const double ut = gV * (X[3] - V * gam);
+                    const double pt2 = ut * ut + pp2; /* (|p~|/m)^2, kept by the collision */
+                    const double gt = sqrt(1.0 + pt2 / c2);
+                    const double ut_new = mu_new * sqrt(pt2);
+                    X[3] = gV * (ut_new + V * gt);
+                    mub = (1.0 - mu_new * mu_new) * pt2 * p->m / (2.0 * Bm);
+                } else {
+                    /* inertial-frame elastic collision: |p| fixed, B at R^{n+1} */
+                    const double pm2 = X[3] * X[3] + 2.0 * mub * Bm / p->m; /* (|p|/m)^2 */
+                    const double pm = sqrt(pm2);
+                    X[3] = mu_new * pm;
+                    mub = (1.0 - mu_new * mu_new) * pm2 * p->m / (2.0 * Bm);
+                }
                 if (p->collision_form == 0)
                     s_rem = -lambda * log(orc_u53(w[2], w[3]));
                 ncoll += 1;
