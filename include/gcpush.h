@@ -68,6 +68,10 @@ typedef struct {
     double charge;          /* particle charge, C (0 selects the electron, -e) */
     double mass;            /* rest mass, kg (0 selects the electron mass) */
     double dt_init;         /* step (s) used to build the start-up history at injection */
+    double wind_u;          /* 0: collisions in the fixed frame, elastic there (default);
+                               > 0: in the frame of a radial solar wind of this speed (m/s),
+                               elastic there (Sect. 3.2, adiabatic cooling): a boost along b
+                               by u.b, the pitch redraw, and the boost back */
 } gc_options;
 
 /* Spherical grid of node values, Sect. 2.2 (trilinear interpolation of the field at the

@@ -394,6 +394,7 @@ int enqueue_advance(gc_ctx *c, cudaStream_t s, double dt, int64_t n_steps, doubl
     P.no_scatter = c->opt.no_scatter;
     P.no_rebirth = c->opt.no_rebirth;
     P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
+    P.wind_u = c->opt.wind_u;
     P.seed = c->opt.seed;
     P.m = c->opt.mass;
     P.c2 = kC * kC;
@@ -633,6 +634,7 @@ gcp::SplitParams split_params(gc_ctx *c, double dt, double lambda_au)
     P.no_scatter = c->opt.no_scatter;
     P.no_rebirth = c->opt.no_rebirth;
     P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
+    P.wind_u = c->opt.wind_u;
     P.seed = c->opt.seed;
     P.m = c->opt.mass;
     P.c2 = kC * kC;
@@ -734,6 +736,8 @@ int gc_create(gc_ctx **out, const gc_options *opt)
         return fail(GC_ERR_INVALID, "gc_create: unknown precision %d", opt->precision);
     if (opt->collision_form < 0 || opt->collision_form > 1 || opt->drift_mask < 0 || opt->drift_mask > 1)
         return fail(GC_ERR_INVALID, "gc_create: bad collision_form/drift_mask");
+    if (!(opt->wind_u >= 0.0) || !(opt->wind_u < 0.01 * kC))
+        return fail(GC_ERR_INVALID, "gc_create: wind_u must be >= 0 and far below c");
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (opt->device < 0 || opt->device >= ndev)

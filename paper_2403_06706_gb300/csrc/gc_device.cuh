@@ -273,6 +273,7 @@ struct Phys {
 template <typename T>
 struct Aux {
     T gamma, vpar, Bm;
+    T b[3]; // unit vector along B (the frame change of wind-frame collisions)
 };
 
 template <typename T>
@@ -404,6 +405,9 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
     aux.gamma = gamma;
     aux.vpar = vpar;
     aux.Bm = Bm;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        aux.b[c] = b[c];
 }
 
 template <typename T>

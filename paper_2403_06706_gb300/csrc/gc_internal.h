@@ -45,6 +45,7 @@ struct PushParams {
     int32_t n_steps;
     int32_t collision_form, no_scatter, no_rebirth;
     double lambda_override; // m, > 0 overrides the ensembles
+    double wind_u;          // m/s, > 0: collisions in the frame of the radial wind (Sect. 3.2)
     uint32_t seed;
     int32_t tally_on;
     double m, c2;           // rest mass (kg), c^2

@@ -209,6 +209,7 @@ extern "C" int gc_advance_noalloc(const gc_options *opt, const gc_grid_desc *g, 
     P.no_scatter = opt->no_scatter;
     P.no_rebirth = opt->no_rebirth;
     P.lambda_override = lambda_au > 0.0 ? lambda_au * kAU : 0.0;
+    P.wind_u = opt->wind_u;
     P.seed = opt->seed;
     P.m = mass;
     P.c2 = kC * kC;

@@ -408,10 +408,27 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
                 const double mu_new = (c.scatter_law == 0) ? 1.0 - 2.0 * a : ((wd.x & 1u) ? -sqrt(a) : sqrt(a));
                 const double Bm = (double)ax.Bm;
                 const double uu = Acc::to(s.U);
-                const double pm2 = uu * uu + 2.0 * (double)s.mub * Bm / P.m;
-                const double pm = sqrt(pm2);
-                s.U = mu_new * pm;
-                s.mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
+                if (P.wind_u > 0.0) {
+                    // Sect. 3.2: elastic in the frame of the wind u = wind_u R/r; the guiding
+                    // centre drifts with u_perp already, so the frame change is a boost along
+                    // b by V = u.b (p_perp unchanged): u~ = gV (u - V gamma), back with -V
+                    const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
+                    const double V = P.wind_u * (X * ax.b[0] + Y * ax.b[1] + Z * ax.b[2]) /
+                                     sqrt(X * X + Y * Y + Z * Z);
+                    const double gV = 1.0 / sqrt(1.0 - V * V / P.c2);
+                    const double pp2 = 2.0 * (double)s.mub * Bm / P.m;
+                    const double gam = sqrt(1.0 + (uu * uu + pp2) / P.c2);
+                    const double ut = gV * (uu - V * gam);
+                    const double pt2 = ut * ut + pp2;
+                    const double gt = sqrt(1.0 + pt2 / P.c2);
+                    s.U = gV * (mu_new * sqrt(pt2) + V * gt);
+                    s.mub = (1.0 - mu_new * mu_new) * pt2 * P.m / (2.0 * Bm);
+                } else {
+                    const double pm2 = uu * uu + 2.0 * (double)s.mub * Bm / P.m;
+                    const double pm = sqrt(pm2);
+                    s.U = mu_new * pm;
+                    s.mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
+                }
                 if (P.collision_form == 0)
                     s.S = -c.lambda * log(u53(wd.z, wd.w));
             } else {
@@ -428,8 +445,23 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
                 }
                 const float Bm = (float)ax.Bm;
                 const float uu = (float)Acc::val(s.U);
-                const float pm2 = uu * uu + 2.0f * (float)s.mub * Bm * (float)ph.inv_m;
-                s.U = df{mu_new * sqrtf(pm2), 0.0f};
+                const float pp2 = 2.0f * (float)s.mub * Bm * (float)ph.inv_m;
+                float pm2 = uu * uu + pp2;
+                if (P.wind_u > 0.0) {
+                    // the wind-frame collision of the FP64 branch above, in float
+                    const float X = Acc::val(s.Rx), Y = Acc::val(s.Ry), Z = Acc::val(s.Rz);
+                    const float V = (float)P.wind_u * (X * ax.b[0] + Y * ax.b[1] + Z * ax.b[2]) *
+                                    rsqrtf(X * X + Y * Y + Z * Z);
+                    const float ic2 = (float)ph.inv_c2;
+                    const float gV = rsqrtf(1.0f - V * V * ic2);
+                    const float gam = sqrtf(1.0f + pm2 * ic2);
+                    const float ut = gV * (uu - V * gam);
+                    pm2 = ut * ut + pp2;
+                    const float gt = sqrtf(1.0f + pm2 * ic2);
+                    s.U = df{gV * (mu_new * sqrtf(pm2) + V * gt), 0.0f};
+                } else {
+                    s.U = df{mu_new * sqrtf(pm2), 0.0f};
+                }
                 s.mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
                 if (P.collision_form == 0)
                     s.S = df{c.lambda_f * neg_log_u(u31(wd.z)), 0.0f};

@@ -79,7 +79,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("seed", C.c_uint32), ("collision_form", C.c_int32), ("drift_mask", C.c_int32),
                 ("no_scatter", C.c_int32), ("no_rebirth", C.c_int32), ("id_base", C.c_uint32),
-                ("charge", C.c_double), ("mass", C.c_double), ("dt_init", C.c_double)]
+                ("charge", C.c_double), ("mass", C.c_double), ("dt_init", C.c_double),
+                ("wind_u", C.c_double)]
 
 
 class GridDesc(C.Structure):
@@ -245,7 +246,7 @@ class Context:
     def __init__(self, precision: int = PREC_FP32_MIXED, device: int = 0, stream=None, seed: int = 0,
                  collision_form: int = 0, drift_mask: int = 0, no_scatter: bool = False,
                  no_rebirth: bool = False, dt_init: float = 0.5, charge: float = 0.0,
-                 mass: float = 0.0, id_base: int = 0):
+                 mass: float = 0.0, id_base: int = 0, wind_u: float = 0.0):
         L = load()
         o = Options()
         o.precision, o.device = precision, device
@@ -255,6 +256,7 @@ class Context:
         o.no_scatter, o.no_rebirth = int(no_scatter), int(no_rebirth)
         o.charge, o.mass, o.dt_init = charge, mass, dt_init
         o.id_base = id_base
+        o.wind_u = wind_u
         h = C.c_void_p()
         _check(L.gc_create(C.byref(h), C.byref(o)), "gc_create")
         self._h = h

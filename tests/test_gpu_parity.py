@@ -246,3 +246,33 @@ def test_plain_fp64_workload_in_full():
     err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes, wl.wind, ens))
     for k, v in err.items():
         assert v < 1e-9, (k, v, err)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_wind_frame_collisions_match_oracle(nodes64, nodes32, precision):
+    """Collisions in the solar-wind frame (Sect. 3.2): the boost along b by u.b, the pitch
+    redraw there and the boost back, against the oracle (many collisions: the second
+    ensemble's mean free path is 0.02 AU)."""
+    calls = [(0.5, 300, 0.0)]
+    u = 4.0e5
+    if precision == "fp64":
+        g, _, gs = run_gpu(nodes64, WIND, ENS, calls, gcpush.PREC_FP64, seed=13, wind_u=u)
+        o, _, os_ = run_oracle(nodes64, WIND, ENS, calls, seed=13, wind_u=u)
+        _ints_equal(g, o)
+        assert gs["collisions"] == os_[0] > 100
+        err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes64, WIND, ENS))
+        for k, v in err.items():
+            assert v < 1e-9, (k, v, err)
+    else:
+        g, _, gs = run_gpu(nodes32, WIND, ENS, calls, gcpush.PREC_FP32_MIXED, seed=13, wind_u=u)
+        o, _, os_ = run_oracle(nodes32, WIND, ENS, calls, seed=13, wind_u=u)
+        div = (g["ncoll"] != o["ncoll"]) | (g["event"] != o["event"]) | (g["t_birth"] != o["t_birth"])
+        assert div.mean() <= 0.02 and os_[0] > 100
+        err = compare_states(g, o.arrays, 1e-4, momentum_scale(o, nodes32, WIND, ENS), skip=div)
+        for k, v in err.items():
+            assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+    # the boost changes the inertial-frame momentum at collisions: compare with the fixed frame
+    g0, _, _ = run_gpu(nodes64 if precision == "fp64" else nodes32, WIND, ENS, calls,
+                       gcpush.PREC_FP64 if precision == "fp64" else gcpush.PREC_FP32_MIXED, seed=13)
+    moved = np.abs(g["u"] - g0["u"]) > 1e-6 * np.abs(g0["u"]).max()
+    assert moved[g["ncoll"] > 0].mean() > 0.9
