@@ -5,8 +5,9 @@
   state agrees bit for bit; after 300 steps the integer state (events, collision counts,
   ids, flags), the tally counts and the counters agree exactly, and the floating-point state
   and the tallied sums of sin^2 alpha to a few FP32 roundings per step (the compiler may
-  contract a product and a sum into one FMA differently in the two kernels): 1e-8 of r for
-  positions, 1e-6 of the scale for the rest.
+  contract a product and a sum into one FMA differently in the two kernels, and a
+  collision's new momentum carries such a difference on): 1e-7 of r for positions, 1e-6 of
+  the scale for the rest. Both with collisions in the fixed frame and in the wind frame.
 * With the neural field the push is compared with the FP64 oracle running the same network
   (oracle.siren_field, BF16 reading): one short run, increments of R and gamma v_par
   measured against their own size. The network's BF16 noise (about 3e-4 RMS and 7e-3 at
