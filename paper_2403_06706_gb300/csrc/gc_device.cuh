@@ -153,6 +153,35 @@ __device__ __forceinline__ void load_node(const double *__restrict__ p, double v
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
 }
 
+// Two FP32 channels in one 64-bit register and the packed f32x2 arithmetic of sm_100+ (two
+// independent IEEE operations per instruction, the same results as two scalar ones).
+__device__ __forceinline__ unsigned long long p2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long p2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long p2_bcast(float x)
+{
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(x));
+    return d;
+}
+
+__device__ __forceinline__ void p2_split(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 // Trilinear interpolation in (r, theta, phi) index space with the index-space gradient of
 // the interpolant (Sect. 2.2). Node-centred grid, poles included in theta, periodic in phi.
 // Positions more than one radial cell outside the grid are flagged; beyond the edge nodes
@@ -201,6 +230,63 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     const uint32_t o0 = (((uint32_t)k * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
     const uint32_t o1 = (((uint32_t)k1 * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
 
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the six channels as three packed pairs (Bx By | Bz Ex | Ey Ez), loaded as
+        // 16 + 8 bytes of each 32-byte node record and interpolated two at a time
+        unsigned long long c2[2][2][2][3];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const float *p = (const float *)gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(p + 8 * a));
+                    c2[b][cc][a][0] = q.x;
+                    c2[b][cc][a][1] = q.y;
+                    c2[b][cc][a][2] = __ldg(reinterpret_cast<const unsigned long long *>(p + 8 * a + 4));
+                }
+            }
+        }
+        const unsigned long long FR = p2_bcast((float)fr), FT = p2_bcast((float)ft), FP = p2_bcast((float)fp);
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {
+            unsigned long long L[2][2], D[2][2];
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    D[b][cc] = p2_sub(c2[b][cc][1][pr], c2[b][cc][0][pr]);
+                    L[b][cc] = p2_fma(FR, D[b][cc], c2[b][cc][0][pr]);
+                }
+            unsigned long long V[2], Dr[2], Dt[2];
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                Dt[cc] = p2_sub(L[1][cc], L[0][cc]);
+                V[cc] = p2_fma(FT, Dt[cc], L[0][cc]);
+                Dr[cc] = p2_fma(FT, p2_sub(D[1][cc], D[0][cc]), D[0][cc]);
+            }
+            const unsigned long long dv = p2_sub(V[1], V[0]);
+            const unsigned long long val = p2_fma(FP, dv, V[0]);
+            const unsigned long long d_r = p2_fma(FP, p2_sub(Dr[1], Dr[0]), Dr[0]);
+            const unsigned long long d_t = p2_fma(FP, p2_sub(Dt[1], Dt[0]), Dt[0]);
+            float v0, v1, r0, r1, t0, t1, p0, p1;
+            p2_split(val, v0, v1);
+            p2_split(d_r, r0, r1);
+            p2_split(d_t, t0, t1);
+            p2_split(dv, p0, p1);
+            const float vv[2] = {v0, v1}, rr[2] = {r0, r1}, tt[2] = {t0, t1}, pp[2] = {p0, p1};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ch = 2 * pr + h;
+                if (ch < 3) {
+                    s.B[ch] = vv[h]; s.dB[0][ch] = rr[h]; s.dB[1][ch] = tt[h]; s.dB[2][ch] = pp[h];
+                } else {
+                    s.E[ch - 3] = vv[h]; s.dE[0][ch - 3] = rr[h]; s.dE[1][ch - 3] = tt[h]; s.dE[2][ch - 3] = pp[h];
+                }
+            }
+        }
+    } else {
     // c[b][cc][a][ch]: a = r offset, b = theta offset, cc = phi offset
     T c[2][2][2][6];
 #pragma unroll
@@ -244,6 +330,7 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
         } else {
             s.E[ch - 3] = val; s.dE[0][ch - 3] = d_r; s.dE[1][ch - 3] = d_t; s.dE[2][ch - 3] = dv;
         }
+    }
     }
 
     // Cartesian gradients of the index coordinates: rhat/dr, thetahat/(r dtheta),
