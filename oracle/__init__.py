@@ -179,12 +179,13 @@ def u53(w_hi: int, w_lo: int) -> float:
 # Fields
 
 
-def grid_field(nodes: np.ndarray, r_min: float, r_max: float, ideal: bool = True) -> Field:
-    """Grid field over node array [n_ph][n_th][n_r][8] (float64 or float32), radii in m."""
+def grid_field(nodes: np.ndarray, r_min: float, r_max: float, ideal=True) -> Field:
+    """Grid field over node array [n_ph][n_th][n_r][8] (float64 or float32), radii in m.
+    ideal: True (E_par = 0), False (E_par = E.b) or 2 (two-fluid: E_par = -b.grad(Phi))."""
     assert nodes.ndim == 4 and nodes.shape[3] == 8 and nodes.flags.c_contiguous
     f = Field()
     f.kind = 0
-    f.ideal = 1 if ideal else 0
+    f.ideal = 2 if ideal == 2 else (1 if ideal else 0)
     f.dtype = 0 if nodes.dtype == np.float64 else 1
     assert nodes.dtype in (np.float64, np.float32)
     f.n_ph, f.n_th, f.n_r = nodes.shape[0], nodes.shape[1], nodes.shape[2]
@@ -223,7 +224,7 @@ def siren_field(params_flat, omega0: float, r_scale: float, B_scale: float, E_sc
             P[o:o + n] = _siren.round_bf16(P[o:o + n])
     f = Field()
     f.kind = 2
-    f.ideal = 1 if ideal else 0
+    f.ideal = 2 if ideal == 2 else (1 if ideal else 0)
     f.siren = P.ctypes.data
     f.siren_omega0, f.siren_rscale, f.siren_Bs, f.siren_Es = omega0, r_scale, B_scale, E_scale
     f.siren_bf16 = 1 if bf16 else 0
@@ -245,10 +246,10 @@ def params(seed: int = 0, q: float = Q_E, m: float = M_E, collision_form: int = 
 
 def field_eval(f: Field, R) -> tuple[dict, int]:
     R = np.ascontiguousarray(R, dtype=np.float64)
-    out = np.zeros(24)
+    out = np.zeros(27)
     fl = lib().orc_field_eval(C.byref(f), _dp(R), _dp(out))
     return {"B": out[0:3], "E": out[3:6], "JB": out[6:15].reshape(3, 3),
-            "JE": out[15:24].reshape(3, 3)}, fl
+            "JE": out[15:24].reshape(3, 3), "gPhi": out[24:27]}, fl
 
 
 def rhs(f: Field, p: Params, X, mub: float):

@@ -63,7 +63,7 @@
 
 typedef struct {
     int32_t kind;     /* 0 = grid, 1 = analytic, 2 = neural (SIREN) */
-    int32_t ideal;    /* 1: E_par := 0 in the RHS */
+    int32_t ideal;    /* 1: E_par := 0 in the RHS; 0: E_par = E.b; 2: E_par = -b.grad(Phi) */
     int32_t dtype;    /* grid node type: 0 = float64, 1 = float32 */
     int32_t n_r, n_th, n_ph;
     int32_t parker_E; /* analytic: add E = -u x B_parker */
@@ -197,6 +197,7 @@ double orc_u53(uint32_t w_hi, uint32_t w_lo)
 typedef struct {
     double B[3], E[3];
     double JB[3][3], JE[3][3];
+    double gPhi[3]; /* gradient of the potential channel (grid kind; 0 otherwise) */
     uint32_t flags;
 } orc_fields;
 
@@ -261,7 +262,7 @@ static void grid_eval(const orc_field *f, const double R[3], orc_fields *o)
     double fp = xp - (double)k;
     k = ((k % f->n_ph) + f->n_ph) % f->n_ph;
 
-    double val[6] = {0}, d_r[6] = {0}, d_t[6] = {0}, d_p[6] = {0};
+    double val[8] = {0}, d_r[8] = {0}, d_t[8] = {0}, d_p[8] = {0};
     for (int a = 0; a < 2; ++a) {
         for (int b = 0; b < 2; ++b) {
             for (int c = 0; c < 2; ++c) {
@@ -270,7 +271,7 @@ static void grid_eval(const orc_field *f, const double R[3], orc_fields *o)
                 const double wt = b ? ft : 1.0 - ft, st = b ? 1.0 : -1.0;
                 const double wp = c ? fp : 1.0 - fp, sp = c ? 1.0 : -1.0;
                 const int64_t base = ((kk * f->n_th + jj) * f->n_r + ii) * 8;
-                for (int ch = 0; ch < 6; ++ch) {
+                for (int ch = 0; ch < 8; ++ch) {
                     const double v = node_value(f, base + ch);
                     val[ch] += wr * wt * wp * v;
                     d_r[ch] += sr * wt * wp * v;
@@ -299,6 +300,9 @@ static void grid_eval(const orc_field *f, const double R[3], orc_fields *o)
         else
             o->E[ch - 3] = val[ch];
     }
+    /* channel 7, the potential Phi of the two-fluid Ohm's law: its Cartesian gradient */
+    for (int jx = 0; jx < 3; ++jx)
+        o->gPhi[jx] = d_r[7] / dr * rhat[jx] + d_t[7] / (dth * r) * that[jx] + d_p[7] / (dph * rho) * phat[jx];
 }
 
 /* Analytic field used by the pins: uniform B and E, a unipolar Parker spiral
@@ -435,12 +439,15 @@ static void siren_eval(const orc_field *f, const double R[3], orc_fields *o)
             o->JB[c][d] = f->siren_Bs * a * a * (J[c][d] / f->siren_rscale - 2.0 * y[c] * R[d] / r2);
             o->JE[c][d] = f->siren_Es * a * (J[3 + c][d] / f->siren_rscale - y[3 + c] * R[d] / r2);
         }
+        /* y_Phi = Phi / (Es AU) */
+        o->gPhi[c] = f->siren_Es * ORC_AU * J[7][c] / f->siren_rscale;
     }
     o->flags = 0;
 }
 
 static void field_eval(const orc_field *f, const double R[3], orc_fields *o)
 {
+    o->gPhi[0] = o->gPhi[1] = o->gPhi[2] = 0.0;
     if (f->kind == 0)
         grid_eval(f, R, o);
     else if (f->kind == 2)
@@ -487,7 +494,9 @@ static void rhs_from_fields(const orc_field *f, const orc_params *p, const orc_f
     /* curvature (b.grad) b */
     for (int i = 0; i < 3; ++i)
         kap[i] = Jb[i][0] * b[0] + Jb[i][1] * b[1] + Jb[i][2] * b[2];
-    const double Epar = f->ideal ? 0.0 : dot(fl->E, b);
+    /* ideal 1: E_par = 0; 0: the interpolated E.b; 2: two-fluid Ohm's law (Sect. 2.2),
+     * E = -u x B - grad(p)/(e n) with p = p(n), i.e. -grad(Phi): E_par = -b.grad(Phi) */
+    const double Epar = f->ideal == 1 ? 0.0 : (f->ideal == 2 ? -dot(fl->gPhi, b) : dot(fl->E, b));
     /* v_E = E x b / B = E x B / B^2 */
     double ExB[3];
     cross(fl->E, fl->B, ExB);
@@ -911,11 +920,12 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
 /* ------------------------------------------------------------------------ */
 /* Single-point entry points for the pins.                                    */
 
-uint32_t orc_field_eval(const orc_field *f, const double R[3], double out[24])
+uint32_t orc_field_eval(const orc_field *f, const double R[3], double out[27])
 {
     orc_fields fl;
     field_eval(f, R, &fl);
     for (int i = 0; i < 3; ++i) {
+        out[24 + i] = fl.gPhi[i];
         out[i] = fl.B[i];
         out[3 + i] = fl.E[i];
         for (int j = 0; j < 3; ++j) {

@@ -17,12 +17,15 @@ to, Sect. 2.1) plus a seeded, exactly divergence-free perturbation:
   g(r) = eps B1 (1 AU / r)^2 sqrt(1 + (Omega r / u_sw)^2), so that the rms of
   dB/|B| is about eps. curl(g A) = g'(r) rhat x A + g curl A.
 * ideal Ohm's law: E = -u x B at every node.
+* optional two-fluid potential (channel Phi): a polytropic wind with n ~ 1/r^2 and
+  p ~ n^G has -grad(p)/(e n) = -grad(Phi) with Phi = phi1 (1 AU / r)^(2 (G - 1)) (phi1: the
+  potential at 1 AU, G = gamma_p); a few hundred volts between the corona and 1 AU.
 
 Node records are 8 channels [Bx, By, Bz, Ex, Ey, Ez, |B|, Phi] (Cartesian
 components, SI units), node-centred, laid out [i_phi][i_theta][i_r][channel]:
 r_i = r_min + i dr, theta_j = j pi / (n_th - 1) (poles included),
 phi_k = 2 pi k / n_ph (periodic). Phi (the two-fluid potential channel) is 0
-for ideal fields. All draws come from numpy's PCG64 with the given seed.
+unless phi1_v is set. All draws come from numpy's PCG64 with the given seed.
 """
 from __future__ import annotations
 
@@ -48,6 +51,8 @@ class WindSpec:
     eps: float = 0.0  # rms dB/|B| of the perturbation
     n_modes: int = 0
     seed: int = 0
+    phi1_v: float = 0.0  # two-fluid potential at 1 AU, V (0: none)
+    gamma_p: float = 1.2  # polytropic index of the potential
 
     @property
     def dr_au(self) -> float:
@@ -130,7 +135,10 @@ def wind_grid(spec: WindSpec, dtype=np.float32) -> np.ndarray:
         out[k, :, :, 0:3] = B
         out[k, :, :, 3:6] = E
         out[k, :, :, 6] = np.sqrt((B * B).sum(-1))
-        out[k, :, :, 7] = 0.0
+        if spec.phi1_v != 0.0:
+            out[k, :, :, 7] = spec.phi1_v * (AU / Rr) ** (2.0 * (spec.gamma_p - 1.0))
+        else:
+            out[k, :, :, 7] = 0.0
     return out
 
 
