@@ -78,13 +78,17 @@ typedef struct {
  * particle position). Node (i_r, i_theta, i_phi) sits at r = r_min + i_r dr
  * (dr = (r_max - r_min)/(n_r - 1)), theta = i_theta pi/(n_th - 1) (poles included),
  * phi = 2 pi i_phi / n_ph (periodic). Layout: [n_ph][n_th][n_r][8] with channels
- * Bx, By, Bz (T), Ex, Ey, Ez (V/m), |B| (T), Phi (V, unused by ideal fields); vector
+ * Bx, By, Bz (T), Ex, Ey, Ez (V/m), |B| (T), Phi (V, used by two-fluid fields only); vector
  * components are Cartesian. */
 typedef struct {
     int32_t n_r, n_th, n_ph;
     int32_t dtype;          /* GC_DTYPE_*; FP32_MIXED contexts convert F64 data to F32 */
     double r_min_au, r_max_au;
-    int32_t ideal;          /* 1: E_par := 0 after interpolation (ideal Ohm's law) */
+    int32_t ideal;          /* 1: E_par := 0 after interpolation (ideal Ohm's law);
+                               0: E_par = E.b of the interpolated E;
+                               2: two-fluid Ohm's law, E = -u x B - grad(p)/(e n) with
+                               p = p(n) (Sect. 2.2): E_par = -b.grad(Phi) from the potential
+                               channel's interpolant (the E channels carry -u x B) */
     int32_t pad0;
 } gc_grid_desc;
 

@@ -806,6 +806,8 @@ int gc_field_load(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_o
         return fail(GC_ERR_INVALID, "gc_field_load: need n_r, n_th, n_ph >= 2");
     if (g->dtype != GC_DTYPE_F64 && g->dtype != GC_DTYPE_F32)
         return fail(GC_ERR_INVALID, "gc_field_load: unknown dtype %d", g->dtype);
+    if (g->ideal < 0 || g->ideal > 2)
+        return fail(GC_ERR_INVALID, "gc_field_load: ideal must be 0, 1 or 2");
     if (!(g->r_min_au > 0.0) || !(g->r_max_au > g->r_min_au))
         return fail(GC_ERR_INVALID, "gc_field_load: need 0 < r_min < r_max");
     const size_t nodes = (size_t)g->n_r * g->n_th * g->n_ph;

@@ -135,6 +135,7 @@ struct Sample {
     T B[3], E[3];
     T dB[3][3], dE[3][3];
     T g[3][3];
+    T dPhi[3]; // derivatives of the potential channel (two-fluid fields only), like dB[d]
     uint32_t flags;
 };
 
@@ -333,6 +334,39 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     }
     }
 
+    // two-fluid fields: the potential channel's index-space gradient (its value is not used)
+    if (gm.ideal == 2) {
+        T ph[2][2][2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const T *p = gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u) + 7;
+                ph[b][cc][0] = __ldg(p);
+                ph[b][cc][1] = __ldg(p + 8);
+            }
+        T L[2][2], D[2][2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                D[b][cc] = ph[b][cc][1] - ph[b][cc][0];
+                L[b][cc] = ph[b][cc][0] + fr * D[b][cc];
+            }
+        T V[2], Dr[2], Dt[2];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            Dt[cc] = L[1][cc] - L[0][cc];
+            V[cc] = L[0][cc] + ft * Dt[cc];
+            Dr[cc] = D[0][cc] + ft * (D[1][cc] - D[0][cc]);
+        }
+        s.dPhi[0] = Dr[0] + fp * (Dr[1] - Dr[0]);
+        s.dPhi[1] = Dt[0] + fp * (Dt[1] - Dt[0]);
+        s.dPhi[2] = V[1] - V[0];
+    } else {
+        s.dPhi[0] = s.dPhi[1] = s.dPhi[2] = T(0);
+    }
+
     // Cartesian gradients of the index coordinates: rhat/dr, thetahat/(r dtheta),
     // phihat/(r sin(theta) dphi)
     const T sr = inv_r * gm.inv_dr;
@@ -455,7 +489,11 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
     for (int c = 0; c < 3; ++c)
         vgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * v_gB * inv_B;
 
-    const T Epar = ideal ? T(0) : dot3(s.E, b);
+    // ideal 1: E_par = 0 (ideal Ohm's law); 0: the interpolated E.b; 2: the two-fluid
+    // correction -grad(Phi) (Sect. 2.2): E_par = -b.grad(Phi) = -sum_d dPhi/di_d (g_d . b)
+    const T Epar = ideal == 1 ? T(0)
+                              : (ideal == 2 ? -(s.dPhi[0] * pb[0] + s.dPhi[1] * pb[1] + s.dPhi[2] * pb[2])
+                                            : dot3(s.E, b));
     // gamma^2 = 1 + (gamma v)^2 / c^2 with (gamma v)^2 = u^2 + 2 mu_B B / m
     const T g2 = T(1) + (u * u + T(2) * mub * Bm * ph.inv_m) * ph.inv_c2;
     const T inv_g = m_rsqrt(g2);

@@ -74,7 +74,7 @@ struct InjectParams {
 //   PRED (all) -> samples -> CORR (all) -> samples -> POST (all; restarts join a list)
 //   -> samples (list) -> R2 (list) -> samples (list) -> R3 (list).
 // INJ_REQ / INJ_FIX redo the field-dependent part of the injection with the samples.
-constexpr int kSampleStride = 36; // B, E, dB, dE (24), g (9), flags (1), pad (2)
+constexpr int kSampleStride = 40; // B, E, dB, dE (24), g (9), flags (1), dPhi (3), pad (3)
 enum SplitKind { SPLIT_PRED = 0, SPLIT_CORR, SPLIT_POST, SPLIT_R2, SPLIT_R3, SPLIT_INJ_REQ, SPLIT_INJ_FIX };
 
 struct SplitParams {

@@ -643,9 +643,9 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
 __device__ __forceinline__ void load_sample(const float *__restrict__ S, int64_t k, int g_in, Sample<float> &s)
 {
     const float4 *q = reinterpret_cast<const float4 *>(S + k * kSampleStride);
-    float v[36];
+    float v[40];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
+    for (int j = 0; j < 10; ++j) {
         const float4 t = __ldg(q + j);
         v[4 * j] = t.x;
         v[4 * j + 1] = t.y;
@@ -656,6 +656,7 @@ __device__ __forceinline__ void load_sample(const float *__restrict__ S, int64_t
     for (int c = 0; c < 3; ++c) {
         s.B[c] = v[c];
         s.E[c] = v[3 + c];
+        s.dPhi[c] = v[34 + c];
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(128) grid_sample_kernel(const GridMeta<float> 
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         Sample<float> s;
         gather(gm, R[3 * k], R[3 * k + 1], R[3 * k + 2], s);
-        float v[36];
+        float v[40];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             v[c] = s.B[c];
@@ -824,11 +825,13 @@ __global__ void __launch_bounds__(128) grid_sample_kernel(const GridMeta<float> 
                 v[24 + 3 * d + c] = s.g[d][c];
             }
         v[33] = __uint_as_float(s.flags);
-        v[34] = 0.f;
-        v[35] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            v[34 + c] = s.dPhi[c];
+        v[37] = v[38] = v[39] = 0.f;
         float4 *q = reinterpret_cast<float4 *>(S + k * kSampleStride);
 #pragma unroll
-        for (int j = 0; j < 9; ++j)
+        for (int j = 0; j < 10; ++j)
             q[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     }
 }

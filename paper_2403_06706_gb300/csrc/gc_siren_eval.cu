@@ -432,6 +432,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             dst[6 + 3 * d + c] = bs * (v[c] * irm - 2.0f * yv[c] * ur);
                             dst[15 + 3 * d + c] = es * (v[3 + c] * irm - yv[3 + c] * ur);
                         }
+                        // the push's layout also takes grad(Phi): Phi = E_scale AU y_Phi
+                        if (p.out.field_stride >= 40)
+                            dst[34 + d] = (float)(p.out.E_scale * au) * v[7] * irm;
                     }
                 }
             }

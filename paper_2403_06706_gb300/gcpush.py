@@ -282,7 +282,8 @@ class Context:
         self.close()
 
     # field -------------------------------------------------------------------
-    def field_load(self, nodes, r_min_au: float, r_max_au: float, ideal: bool = True):
+    def field_load(self, nodes, r_min_au: float, r_max_au: float, ideal=True):
+        """ideal: True (E_par = 0), False (E_par = E.b) or 2 (two-fluid: E_par = -b.grad(Phi))."""
         """nodes: [n_ph][n_th][n_r][8] float32/float64, numpy (host) or torch CUDA tensor."""
         g = GridDesc()
         on_dev = 0
@@ -299,7 +300,8 @@ class Context:
             g.n_ph, g.n_th, g.n_r = nodes.shape[:3]
             g.dtype = DTYPE_F64 if nodes.dtype == np.float64 else DTYPE_F32
             ptr = C.c_void_p(nodes.ctypes.data)
-        g.r_min_au, g.r_max_au, g.ideal = r_min_au, r_max_au, int(ideal)
+        g.r_min_au, g.r_max_au = r_min_au, r_max_au
+        g.ideal = 2 if ideal == 2 else (1 if ideal else 0)
         _check(load().gc_field_load(self._h, C.byref(g), ptr, on_dev), "gc_field_load")
         self._grid_keep = nodes
 

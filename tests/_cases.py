@@ -23,11 +23,11 @@ def oracle_ensembles(ens):
 
 
 def run_gpu(nodes, wind, ens, calls, precision, seed=0, tally=None, dt_init=None, launch=None,
-            **opt):
+            ideal=True, **opt):
     """calls: list of (dt, n_steps, lambda_au). Returns (state, tallies, stats)."""
     dt0 = dt_init if dt_init is not None else calls[0][0]
     with gcpush.Context(precision=precision, device=0, seed=seed, dt_init=dt0, **opt) as ctx:
-        ctx.field_load(nodes, wind.r_min_au, wind.r_max_au)
+        ctx.field_load(nodes, wind.r_min_au, wind.r_max_au, ideal=ideal)
         ctx.inject(ens)
         if launch:
             ctx.set_launch(**launch)
@@ -52,8 +52,8 @@ def tally_spec(t: dict) -> oracle.TallySpec:
 
 
 def run_oracle(nodes, wind, ens, calls, seed=0, tally=None, dt_init=None, subset=None,
-               n_threads=0, **opt):
-    f = oracle.grid_field(nodes, wind.r_min_au * AU, wind.r_max_au * AU)
+               n_threads=0, ideal=True, **opt):
+    f = oracle.grid_field(nodes, wind.r_min_au * AU, wind.r_max_au * AU, ideal=ideal)
     p = oracle.params(seed=seed, **opt)
     oe = oracle_ensembles(ens)
     dt0 = dt_init if dt_init is not None else calls[0][0]

@@ -276,3 +276,31 @@ def test_wind_frame_collisions_match_oracle(nodes64, nodes32, precision):
                        gcpush.PREC_FP64 if precision == "fp64" else gcpush.PREC_FP32_MIXED, seed=13)
     moved = np.abs(g["u"] - g0["u"]) > 1e-6 * np.abs(g0["u"]).max()
     assert moved[g["ncoll"] > 0].mean() > 0.9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_two_fluid_field_matches_oracle(precision):
+    """The two-fluid Ohm's law (Sect. 2.2): E_par = -b.grad(Phi) from the potential channel
+    of a polytropic wind (500 V at 1 AU), against the oracle; the parallel force must change
+    the trajectories relative to the ideal field."""
+    w = synth.WindSpec(64, 32, 64, phi1_v=500.0)
+    dtype = np.float64 if precision == "fp64" else np.float32
+    prec = gcpush.PREC_FP64 if precision == "fp64" else gcpush.PREC_FP32_MIXED
+    nodes = synth.wind_grid(w, dtype=dtype)
+    calls = [(0.5, 300, 0.0)]
+    g, _, gs = run_gpu(nodes, w, ENS, calls, prec, seed=19, ideal=2)
+    o, _, os_ = run_oracle(nodes, w, ENS, calls, seed=19, ideal=2)
+    if precision == "fp64":
+        _ints_equal(g, o)
+        err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes, w, ENS))
+        for k, v in err.items():
+            assert v < 1e-9, (k, v, err)
+    else:
+        div = (g["ncoll"] != o["ncoll"]) | (g["event"] != o["event"]) | (g["t_birth"] != o["t_birth"])
+        assert div.mean() <= 0.02
+        err = compare_states(g, o.arrays, 1e-4, momentum_scale(o, nodes, w, ENS), skip=div)
+        for k, v in err.items():
+            assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+    gi, _, _ = run_gpu(nodes, w, ENS, calls, prec, seed=19, ideal=True)
+    pm = momentum_scale(o, nodes, w, ENS)
+    assert np.abs(g["u"] - gi["u"]).max() > 1e-7 * pm.max()

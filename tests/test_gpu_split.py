@@ -7,7 +7,8 @@
   and the tallied sums of sin^2 alpha to a few FP32 roundings per step (the compiler may
   contract a product and a sum into one FMA differently in the two kernels, and a
   collision's new momentum carries such a difference on): 1e-7 of r for positions, 1e-6 of
-  the scale for the rest. Both with collisions in the fixed frame and in the wind frame.
+  the scale for the rest. With collisions in the fixed frame and in the wind frame, and with
+  the two-fluid parallel field.
 * With the neural field the push is compared with the FP64 oracle running the same network
   (oracle.siren_field, BF16 reading): one short run, increments of R and gamma v_par
   measured against their own size. The network's BF16 noise (about 3e-4 RMS and 7e-3 at
@@ -31,9 +32,9 @@ ENS = (synth.EnsembleSpec(700, lam_au=0.05, r_out_au=2.4),
 TALLY = dict(cadence=25, n_mu=8, n_E=8, n_r=16, n_age=8, age_max_s=500.0)
 
 
-def _run(source, nodes, n_steps=150, calls=2, wind_u=0.0):
+def _run(source, nodes, n_steps=150, calls=2, wind_u=0.0, ideal=True):
     with gcpush.Context(precision=gcpush.PREC_FP32_MIXED, seed=17, wind_u=wind_u) as c:
-        c.field_load(nodes, WIND.r_min_au, WIND.r_max_au)
+        c.field_load(nodes, WIND.r_min_au, WIND.r_max_au, ideal=ideal)
         c.set_launch(block=128, steps_per_launch=n_steps, sort_every=0)
         if source != gcpush.FIELD_GRID:
             c.field_select(source)
@@ -45,11 +46,12 @@ def _run(source, nodes, n_steps=150, calls=2, wind_u=0.0):
         return st0, c.get_state(), c.tally_read(), c.stats()
 
 
-@pytest.mark.parametrize("wind_u", [0.0, 4.0e5])
-def test_grid_sampled_split_push_reproduces_fused_push(wind_u):
-    nodes = synth.wind_grid(WIND, dtype=np.float32)
-    a0, a, ta, sa = _run(gcpush.FIELD_GRID, nodes, wind_u=wind_u)
-    b0, b, tb, sb = _run(gcpush.FIELD_GRID_SAMPLED, nodes, wind_u=wind_u)
+@pytest.mark.parametrize("wind_u,ideal", [(0.0, True), (4.0e5, True), (0.0, 2)])
+def test_grid_sampled_split_push_reproduces_fused_push(wind_u, ideal):
+    spec = WIND if ideal is True else synth.WindSpec(64, 32, 64, eps=0.1, n_modes=4, phi1_v=500.0)
+    nodes = synth.wind_grid(spec, dtype=np.float32)
+    a0, a, ta, sa = _run(gcpush.FIELD_GRID, nodes, wind_u=wind_u, ideal=ideal)
+    b0, b, tb, sb = _run(gcpush.FIELD_GRID_SAMPLED, nodes, wind_u=wind_u, ideal=ideal)
     for k in a0:
         np.testing.assert_array_equal(a0[k], b0[k], err_msg="after injection: " + k)
     r = np.sqrt(a["x"] ** 2 + a["y"] ** 2 + a["z"] ** 2)
