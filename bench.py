@@ -305,6 +305,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-neural", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--neural-particles", type=int, default=10_000_000)
     ap.add_argument("--neural-epochs", type=int, default=None)
     ap.add_argument("--particles", type=int, default=3_000_000,
@@ -465,6 +466,34 @@ def main():
                    "push_steps_per_call": nb_steps, "graph": True, "autotune": choice}
         cb.close()
 
+    # ---------------- method variants on the same workload (Sect. 3.2, Sect. 2.2) -------------
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        nodes_tf = nodes.copy()
+        nodes_tf[..., 7] = synth.potential_of(wl.wind, 500.0)[None, None, :].astype(nodes.dtype)
+        for name, opt, grid, ideal in (("wind_frame_collisions", {"wind_u": 4.0e5}, nodes, True),
+                                       ("two_fluid_field", {}, nodes_tf, 2)):
+            cv = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wl.seed,
+                                dt_init=wl.dt, id_base=shard.id_base(rank, n_rank), **opt)
+            cv.field_load(grid, wl.wind.r_min_au, wl.wind.r_max_au, ideal=ideal)
+            cv.inject(list(wl.ensembles))
+            cv.set_launch(**LAUNCH)
+            cv.tally_arm(**TALLY)
+            cv.advance(wl.dt, PUSH_STEPS)
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(2):
+                cv.advance(wl.dt, PUSH_STEPS)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = {"value": world * n_rank * PUSH_STEPS * 2 / (v0.elapsed_time(v1) / 1e3),
+                              "unit": UNIT, "push_steps": 2 * PUSH_STEPS,
+                              "collisions": cv.stats()["collisions"]}
+            cv.close()
+
     neural = None
     if not args.no_neural:
         neural = neural_bench(args, nodes, local, stream, rank)
@@ -482,7 +511,8 @@ def main():
             "config": config_dict(wl, n_rank),
             "parallelism": f"particles sharded by id, {world} GPU(s), no data-path collective",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clocks, "fp64_plain": fp64, "batched": batched, "neural": neural,
+            "clocks": clocks, "fp64_plain": fp64, "batched": batched, "variants": variants,
+            "neural": neural,
             "accuracy": "FP32 path within 1e-4 of the FP64 oracle over the first 1e3 steps; "
                         "FP64 path within 1e-9 (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)",
         }

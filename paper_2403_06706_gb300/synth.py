@@ -117,6 +117,12 @@ def wind_at(spec: WindSpec, X: np.ndarray, modes=None) -> tuple[np.ndarray, np.n
     return B, E
 
 
+def potential_of(spec: WindSpec, phi1_v: float, gamma_p: float = 1.2) -> np.ndarray:
+    """The polytropic potential channel (see module doc) on the radial nodes, shape (n_r,)."""
+    r = (spec.r_min_au + spec.dr_au * np.arange(spec.n_r)) * AU
+    return phi1_v * (AU / r) ** (2.0 * (gamma_p - 1.0))
+
+
 def wind_grid(spec: WindSpec, dtype=np.float32) -> np.ndarray:
     """Node array [n_ph][n_th][n_r][8] of the synthetic wind (see module doc)."""
     r = (spec.r_min_au + spec.dr_au * np.arange(spec.n_r)) * AU
