@@ -71,7 +71,7 @@ class Field(C.Structure):
         ("dipole_m", C.c_double * 3),
         ("siren", C.c_void_p), ("siren_omega0", C.c_double), ("siren_rscale", C.c_double),
         ("siren_Bs", C.c_double), ("siren_Es", C.c_double), ("siren_bf16", C.c_int32),
-        ("pad1", C.c_int32),
+        ("pad1", C.c_int32), ("nodes1", C.c_void_p), ("t_snap0", C.c_double), ("t_snap1", C.c_double),
     ]
 
 
@@ -132,9 +132,9 @@ def lib():
         L.orc_philox4x32_10.restype = None
         L.orc_u53.argtypes = [C.c_uint32, C.c_uint32]
         L.orc_u53.restype = C.c_double
-        L.orc_field_eval.argtypes = [C.POINTER(Field), _DP, _DP]
+        L.orc_field_eval.argtypes = [C.POINTER(Field), _DP, C.c_double, _DP]
         L.orc_field_eval.restype = C.c_uint32
-        L.orc_rhs.argtypes = [C.POINTER(Field), C.POINTER(Params), _DP, C.c_double, _DP, _DP]
+        L.orc_rhs.argtypes = [C.POINTER(Field), C.POINTER(Params), _DP, C.c_double, C.c_double, _DP, _DP]
         L.orc_rhs.restype = C.c_uint32
         L.orc_predictor.argtypes = [_DP, _DP, _DP, C.c_double, C.c_double, _DP]
         L.orc_corrector.argtypes = [_DP, _DP, _DP, _DP, C.c_double, C.c_double, _DP]
@@ -244,21 +244,35 @@ def params(seed: int = 0, q: float = Q_E, m: float = M_E, collision_form: int = 
     return p
 
 
-def field_eval(f: Field, R) -> tuple[dict, int]:
+def field_eval(f: Field, R, t: float = 0.0) -> tuple[dict, int]:
     R = np.ascontiguousarray(R, dtype=np.float64)
-    out = np.zeros(27)
-    fl = lib().orc_field_eval(C.byref(f), _dp(R), _dp(out))
+    out = np.zeros(33)
+    fl = lib().orc_field_eval(C.byref(f), _dp(R), float(t), _dp(out))
     return {"B": out[0:3], "E": out[3:6], "JB": out[6:15].reshape(3, 3),
-            "JE": out[15:24].reshape(3, 3), "gPhi": out[24:27]}, fl
+            "JE": out[15:24].reshape(3, 3), "gPhi": out[24:27], "dBdt": out[27:30],
+            "dEdt": out[30:33]}, fl
 
 
-def rhs(f: Field, p: Params, X, mub: float):
-    """F(X) of Eqs. 1-2 and (gamma, v_par, |B|, E_par)."""
+def rhs(f: Field, p: Params, X, mub: float, t: float = 0.0):
+    """F(X, t) of Eqs. 1-2 and (gamma, v_par, |B|, E_par)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     F = np.zeros(4)
     aux = np.zeros(4)
-    fl = lib().orc_rhs(C.byref(f), C.byref(p), _dp(X), float(mub), _dp(F), _dp(aux))
+    fl = lib().orc_rhs(C.byref(f), C.byref(p), _dp(X), float(t), float(mub), _dp(F), _dp(aux))
     return F, aux, fl
+
+
+def grid_field_pair(nodes0: np.ndarray, nodes1: np.ndarray, t0: float, t1: float, r_min: float, r_max: float,
+                    ideal=True) -> Field:
+    """Two grid snapshots at times t0 < t1 (s): the field is linear in time between them and
+    held outside."""
+    assert nodes1.shape == nodes0.shape and nodes1.dtype == nodes0.dtype and nodes1.flags.c_contiguous
+    assert t1 > t0
+    f = grid_field(nodes0, r_min, r_max, ideal)
+    f.nodes1 = nodes1.ctypes.data
+    f.t_snap0, f.t_snap1 = t0, t1
+    f._keep1 = nodes1
+    return f
 
 
 def predictor(X, F0, F1, dt, tau):

@@ -84,6 +84,10 @@ typedef struct {
     double siren_omega0, siren_rscale, siren_Bs, siren_Es;
     int32_t siren_bf16; /* 1: the values carried between layers are rounded to bfloat16 */
     int32_t pad1;
+    /* kind 0 with nodes1 set: a second snapshot; the field is linear in time between the
+     * snapshots at t_snap0 < t_snap1 (held constant outside) */
+    const void *nodes1;
+    double t_snap0, t_snap1;
 } orc_field;
 
 typedef struct {
@@ -198,6 +202,7 @@ typedef struct {
     double B[3], E[3];
     double JB[3][3], JE[3][3];
     double gPhi[3]; /* gradient of the potential channel (grid kind; 0 otherwise) */
+    double dBdt[3], dEdt[3]; /* time derivatives (two snapshots; 0 otherwise) */
     uint32_t flags;
 } orc_fields;
 
@@ -445,11 +450,48 @@ static void siren_eval(const orc_field *f, const double R[3], orc_fields *o)
     o->flags = 0;
 }
 
-static void field_eval(const orc_field *f, const double R[3], orc_fields *o)
+/* Two snapshots: every quantity linear in time between them, d/dt the secant slope. */
+static void grid_eval_t(const orc_field *f, const double R[3], double t, orc_fields *o)
+{
+    grid_eval(f, R, o);
+    if (!f->nodes1)
+        return;
+    orc_field f1 = *f;
+    f1.nodes = f->nodes1;
+    orc_fields o1;
+    o1.gPhi[0] = o1.gPhi[1] = o1.gPhi[2] = 0.0;
+    grid_eval(&f1, R, &o1);
+    const double span = f->t_snap1 - f->t_snap0;
+    double w = (t - f->t_snap0) / span;
+    int inside = 1;
+    if (w < 0.0) {
+        w = 0.0;
+        inside = 0;
+    } else if (w > 1.0) {
+        w = 1.0;
+        inside = 0;
+    }
+    for (int i = 0; i < 3; ++i) {
+        o->dBdt[i] = inside ? (o1.B[i] - o->B[i]) / span : 0.0;
+        o->dEdt[i] = inside ? (o1.E[i] - o->E[i]) / span : 0.0;
+        o->B[i] = (1.0 - w) * o->B[i] + w * o1.B[i];
+        o->E[i] = (1.0 - w) * o->E[i] + w * o1.E[i];
+        o->gPhi[i] = (1.0 - w) * o->gPhi[i] + w * o1.gPhi[i];
+        for (int j = 0; j < 3; ++j) {
+            o->JB[i][j] = (1.0 - w) * o->JB[i][j] + w * o1.JB[i][j];
+            o->JE[i][j] = (1.0 - w) * o->JE[i][j] + w * o1.JE[i][j];
+        }
+    }
+    o->flags |= o1.flags;
+}
+
+static void field_eval(const orc_field *f, const double R[3], double t, orc_fields *o)
 {
     o->gPhi[0] = o->gPhi[1] = o->gPhi[2] = 0.0;
+    for (int i = 0; i < 3; ++i)
+        o->dBdt[i] = o->dEdt[i] = 0.0;
     if (f->kind == 0)
-        grid_eval(f, R, o);
+        grid_eval_t(f, R, t, o);
     else if (f->kind == 2)
         siren_eval(f, R, o);
     else
@@ -523,14 +565,30 @@ static void rhs_from_fields(const orc_field *f, const orc_params *p, const orc_f
     const double gamma = sqrt(1.0 + (u * u + 2.0 * mub * Bm / m) / c2);
     const double vpar = u / gamma;
 
-    /* Eq. 1 */
+    /* time-dependent fields (the terms of the GCA equations that vanish for the paper's
+     * steady wind): db/dt = (dB/dt - b (b.dB/dt)) / B,
+     * dv_E/dt = (dE/dt x B + E x dB/dt) / B^2 - 2 v_E (b.dB/dt) / B */
+    double db_dt[3], dvE_dt[3];
+    {
+        const double bdB = dot(b, fl->dBdt);
+        double t1[3], t2[3];
+        cross(fl->dEdt, fl->B, t1);
+        cross(fl->E, fl->dBdt, t2);
+        for (int i = 0; i < 3; ++i) {
+            db_dt[i] = (fl->dBdt[i] - b[i] * bdB) / Bm;
+            dvE_dt[i] = (t1[i] + t2[i]) / (Bm * Bm) - 2.0 * vE[i] * bdB / Bm;
+        }
+    }
+
+    /* Eq. 1, with v_par db/dt + dv_E/dt in the bracket for time-dependent fields */
     double br[3];
     for (int i = 0; i < 3; ++i)
         br[i] = mub / (gamma * gamma * m) * gB[i]
                 + (q * vpar * Epar / (gamma * m * c2)) * vE[i]
                 + vpar * vpar * kap[i]
                 + vpar * (vE_grad_b[i] + b_grad_vE[i])
-                + vE_grad_vE[i];
+                + vE_grad_vE[i]
+                + vpar * db_dt[i] + dvE_dt[i];
     double bxbr[3];
     cross(b, br, bxbr);
     const double pre = gamma * m / (q * Bm);
@@ -544,7 +602,7 @@ static void rhs_from_fields(const orc_field *f, const orc_params *p, const orc_f
     /* Eq. 2 */
     double w[3];
     for (int i = 0; i < 3; ++i)
-        w[i] = vpar * kap[i] + vE_grad_b[i];
+        w[i] = vpar * kap[i] + vE_grad_b[i] + db_dt[i];
     if (p->drift_mask == 1)
         F[3] = (q / m) * Epar - mub / (gamma * m) * dot(b, gB);
     else
@@ -559,11 +617,11 @@ static void rhs_from_fields(const orc_field *f, const orc_params *p, const orc_f
     }
 }
 
-static uint32_t rhs(const orc_field *f, const orc_params *p, const double X[4], double mub,
+static uint32_t rhs(const orc_field *f, const orc_params *p, const double X[4], double t, double mub,
                     double F[4], orc_aux *aux)
 {
     orc_fields fl;
-    field_eval(f, X, &fl);
+    field_eval(f, X, t, &fl);
     rhs_from_fields(f, p, &fl, X, mub, F, aux);
     return fl.flags;
 }
@@ -608,18 +666,18 @@ static void store(orc_state *s, int64_t i, const double X[4], const double F0[4]
     }
 }
 
-/* Start-up of the two-level history (Sect. 2.2): F^n = F(X^n),
- * X^{n-1} = X^n - dt F^n, F^{n-1} = F(X^{n-1}).                              */
-static uint32_t restart(const orc_field *f, const orc_params *p, const double X[4], double mub,
+/* Start-up of the two-level history (Sect. 2.2): F^n = F(X^n, t),
+ * X^{n-1} = X^n - dt F^n, F^{n-1} = F(X^{n-1}, t - dt).                     */
+static uint32_t restart(const orc_field *f, const orc_params *p, const double X[4], double t, double mub,
                         double dt, double F0[4], double F1[4], double *vpar)
 {
     orc_aux aux;
-    uint32_t fl = rhs(f, p, X, mub, F0, &aux);
+    uint32_t fl = rhs(f, p, X, t, mub, F0, &aux);
     *vpar = aux.vpar;
     double Xm[4];
     for (int c = 0; c < 4; ++c)
         Xm[c] = X[c] - dt * F0[c];
-    fl |= rhs(f, p, Xm, mub, F1, NULL);
+    fl |= rhs(f, p, Xm, t - dt, mub, F1, NULL);
     return fl;
 }
 
@@ -676,12 +734,12 @@ int orc_inject(const orc_field *f, const orc_params *p, const orc_ensemble *ens,
         X[1] = E->r0 * cos(E->lat) * sin(E->lon);
         X[2] = E->r0 * sin(E->lat);
         orc_fields fl;
-        field_eval(f, X, &fl);
+        field_eval(f, X, t0, &fl);
         const double Bm = sqrt(dot(fl.B, fl.B));
         X[3] = mu0 * pm;
         const double mub = (1.0 - mu0 * mu0) * pm * pm * p->m / (2.0 * Bm);
         double F0[4], F1[4], vpar;
-        uint32_t flg = fl.flags | restart(f, p, X, mub, dt, F0, F1, &vpar);
+        uint32_t flg = fl.flags | restart(f, p, X, t0, mub, dt, F0, F1, &vpar);
         store(s, i, X, F0, F1);
         s->mub[i] = mub;
         s->vpar[i] = vpar;
@@ -801,9 +859,10 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
             double Xs[4], Fs[4], X1[4], Fn1[4];
             orc_aux aux1;
             orc_predictor(X, F0, F1, dt, tau, Xs);
-            flags |= rhs(f, p, Xs, mub, Fs, NULL);
+            /* both evaluations of the step are at the step's end time t^{n+1} */
+            flags |= rhs(f, p, Xs, t_new, mub, Fs, NULL);
             orc_corrector(X, F0, F1, Fs, dt, tau, X1);
-            flags |= rhs(f, p, X1, mub, Fn1, &aux1);
+            flags |= rhs(f, p, X1, t_new, mub, Fn1, &aux1);
 
             const double ds = dt * (fabs(vpar0) + fabs(aux1.vpar)) / 2.0;
             const double r1 = sqrt(X1[0] * X1[0] + X1[1] * X1[1] + X1[2] * X1[2]);
@@ -836,7 +895,7 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
                 s_rem = -lambda * log(orc_u53(w[2], w[3]));
                 ncoll = 0;
                 t_birth = t_new;
-                flags |= restart(f, p, X, mub, dt, F0, F1, &vpar0);
+                flags |= restart(f, p, X, t_new, mub, dt, F0, F1, &vpar0);
                 h_prev = dt;
                 n_reb += 1;
             } else if (collide) {
@@ -877,7 +936,7 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
                     s_rem = -lambda * log(orc_u53(w[2], w[3]));
                 ncoll += 1;
                 n_coll += 1;
-                flags |= restart(f, p, X, mub, dt, F0, F1, &vpar0);
+                flags |= restart(f, p, X, t_new, mub, dt, F0, F1, &vpar0);
                 h_prev = dt;
             } else {
                 for (int c = 0; c < 4; ++c) {
@@ -894,7 +953,7 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
             if (T && T->cadence > 0 && ((step0 + k + 1) % T->cadence) == 0
                 && t_birth >= T->t_start) {
                 orc_fields fl;
-                field_eval(f, X, &fl);
+                field_eval(f, X, t_new, &fl);
                 const double Bm = sqrt(dot(fl.B, fl.B));
                 tally_sample(T, p, s->ens[i], X, mub, Bm, t_new - t_birth, ncoll);
             }
@@ -920,12 +979,14 @@ int orc_advance(const orc_field *f, const orc_params *p, const orc_ensemble *ens
 /* ------------------------------------------------------------------------ */
 /* Single-point entry points for the pins.                                    */
 
-uint32_t orc_field_eval(const orc_field *f, const double R[3], double out[27])
+uint32_t orc_field_eval(const orc_field *f, const double R[3], double t, double out[33])
 {
     orc_fields fl;
-    field_eval(f, R, &fl);
+    field_eval(f, R, t, &fl);
     for (int i = 0; i < 3; ++i) {
         out[24 + i] = fl.gPhi[i];
+        out[27 + i] = fl.dBdt[i];
+        out[30 + i] = fl.dEdt[i];
         out[i] = fl.B[i];
         out[3 + i] = fl.E[i];
         for (int j = 0; j < 3; ++j) {
@@ -936,11 +997,11 @@ uint32_t orc_field_eval(const orc_field *f, const double R[3], double out[27])
     return fl.flags;
 }
 
-uint32_t orc_rhs(const orc_field *f, const orc_params *p, const double X[4], double mub,
+uint32_t orc_rhs(const orc_field *f, const orc_params *p, const double X[4], double t, double mub,
                  double F[4], double aux_out[4])
 {
     orc_aux aux;
-    uint32_t fl = rhs(f, p, X, mub, F, &aux);
+    uint32_t fl = rhs(f, p, X, t, mub, F, &aux);
     if (aux_out) {
         aux_out[0] = aux.gamma;
         aux_out[1] = aux.vpar;
