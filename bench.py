@@ -15,6 +15,7 @@ the 129 MB L2, so no flush is needed between steps.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -472,11 +473,19 @@ def main():
         variants = {}
         nodes_tf = nodes.copy()
         nodes_tf[..., 7] = synth.potential_of(wl.wind, 500.0)[None, None, :].astype(nodes.dtype)
-        for name, opt, grid, ideal in (("wind_frame_collisions", {"wind_u": 4.0e5}, nodes, True),
-                                       ("two_fluid_field", {}, nodes_tf, 2)):
+        # a time-dependent field: the wind turning faster and stronger (5e5 m/s, 4.2 nT at
+        # 1 AU, another perturbation) over the variant's whole run, two snapshots blended in time
+        nodes_t1 = synth.wind_grid(dataclasses.replace(wl.wind, B1=4.2e-9, u_sw=5.0e5, seed=wl.wind.seed + 1),
+                                   dtype=nodes.dtype)
+        window = (0.0, 3 * PUSH_STEPS * wl.dt)
+        for name, opt, grid, ideal, grid1 in (("wind_frame_collisions", {"wind_u": 4.0e5}, nodes, True, None),
+                                              ("two_fluid_field", {}, nodes_tf, 2, None),
+                                              ("time_dependent_field", {}, nodes, True, nodes_t1)):
             cv = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wl.seed,
                                 dt_init=wl.dt, id_base=shard.id_base(rank, n_rank), **opt)
             cv.field_load(grid, wl.wind.r_min_au, wl.wind.r_max_au, ideal=ideal)
+            if grid1 is not None:
+                cv.field_load_next(grid1, *window)
             cv.inject(list(wl.ensembles))
             cv.set_launch(**LAUNCH)
             cv.tally_arm(**TALLY)

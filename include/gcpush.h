@@ -177,6 +177,17 @@ const char *gc_last_error(void);
  * data_on_device != 0 (then read on the context's stream). */
 int gc_field_load(gc_ctx *ctx, const gc_grid_desc *g, const void *data, int data_on_device);
 
+/* Make the loaded field time dependent (Eqs. 1-2 keep their time-derivative terms, Sect. 2):
+ * data is a second snapshot on the same grid, with the same layout, dtype and descriptor as
+ * the last gc_field_load, and [t0_s, t1_s] the simulated times of the two snapshots. Every
+ * field evaluation then blends the two linearly in time, and the derivatives dB/dt and dE/dt
+ * are the snapshots' difference over (t1_s - t0_s). Outside the window the field holds the
+ * nearer snapshot and its time derivatives are zero. The context copies the data (and converts it to its precision); a later
+ * gc_field_load makes the field steady again. GC_ERR_STATE without a first snapshot,
+ * GC_ERR_INVALID unless t0_s < t1_s are finite, GC_ERR_UNSUPPORTED while a split-step field
+ * source (gc_field_select) is selected. */
+int gc_field_load_next(gc_ctx *ctx, const void *data, int data_on_device, double t0_s, double t1_s);
+
 /* Inject the ensembles (Sect. 3) at the current time; needs a loaded field. Each
  * particle's mu0 (and energy for a spectrum) comes from Philox events 0 and 1 of its
  * stream; its free path is drawn, and the start-up history is built with dt_init. */

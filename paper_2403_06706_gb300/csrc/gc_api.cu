@@ -116,8 +116,9 @@ struct gc_ctx {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
 
-    // field
+    // field (d_grid1: the second snapshot of a time-dependent field)
     void *d_grid = nullptr;
+    void *d_grid1 = nullptr;
     gc_grid_desc grid{};
     gcp::GridHost gh{};
     bool has_field = false;
@@ -368,7 +369,7 @@ int push_grid(gc_ctx *c)
 {
     int &nb = c->blocks_per_sm[c->block / 32];
     if (nb <= 0) {
-        nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block);
+        nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block, c->gh.nodes1 != nullptr);
         cudaGetLastError(); // an occupancy query failure only means "one block"
         if (nb < 1) nb = 1;
     }
@@ -709,6 +710,39 @@ int split_inject_fix(gc_ctx *c, int64_t slot0, int64_t n_new)
     return GC_OK;
 }
 
+// copy (and convert to the context's precision) node data into a new device array
+int upload_nodes(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_on_device, void **dst)
+{
+    const size_t nval = (size_t)g->n_r * g->n_th * g->n_ph * 8;
+    const bool want64 = (c->opt.precision == GC_PREC_FP64);
+    const size_t esz = want64 ? sizeof(double) : sizeof(float);
+    const size_t in_esz = (g->dtype == GC_DTYPE_F64) ? sizeof(double) : sizeof(float);
+    CUDA_TRY(cudaMalloc(dst, nval * esz));
+    const bool same = (want64 == (g->dtype == GC_DTYPE_F64));
+    const cudaMemcpyKind kind = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (same) {
+        CUDA_TRY(cudaMemcpyAsync(*dst, data, nval * esz, kind, c->stream));
+    } else {
+        void *tmp = nullptr;
+        CUDA_TRY(cudaMalloc(&tmp, nval * in_esz));
+        cudaError_t e = cudaMemcpyAsync(tmp, data, nval * in_esz, kind, c->stream);
+        if (e == cudaSuccess) {
+            if (want64)
+                convert_nodes<<<1024, 256, 0, c->stream>>>((const float *)tmp, (double *)*dst, nval);
+            else
+                convert_nodes<<<1024, 256, 0, c->stream>>>((const double *)tmp, (float *)*dst, nval);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess)
+            return fail(GC_ERR_CUDA, "node upload: %s", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GC_OK;
+}
+
 void free_tally(gc_ctx *c)
 {
     if (c->d_tally) cudaFree(c->d_tally);
@@ -779,6 +813,7 @@ void gc_destroy(gc_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     if (c->d_grid) cudaFree(c->d_grid);
+    if (c->d_grid1) cudaFree(c->d_grid1);
     free_state(c->st);
     if (c->d_ens) cudaFree(c->d_ens);
     free_tally(c);
@@ -816,8 +851,6 @@ int gc_field_load(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_o
         return fail(GC_ERR_INVALID, "gc_field_load: %zu node values exceed the 2^32 index range", nval);
     TRY(set_device(c));
     const bool want64 = (c->opt.precision == GC_PREC_FP64);
-    const size_t esz = want64 ? sizeof(double) : sizeof(float);
-    const size_t in_esz = (g->dtype == GC_DTYPE_F64) ? sizeof(double) : sizeof(float);
     drop_graphs(c);
     if (c->d_grid) {
         CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -825,28 +858,13 @@ int gc_field_load(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_o
         c->d_grid = nullptr;
         c->has_field = false;
     }
-    CUDA_TRY(cudaMalloc(&c->d_grid, nval * esz));
-    const bool same = (want64 == (g->dtype == GC_DTYPE_F64));
-    const cudaMemcpyKind kind = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (same) {
-        CUDA_TRY(cudaMemcpyAsync(c->d_grid, data, nval * esz, kind, c->stream));
-    } else {
-        void *tmp = nullptr;
-        CUDA_TRY(cudaMalloc(&tmp, nval * in_esz));
-        cudaError_t e = cudaMemcpyAsync(tmp, data, nval * in_esz, kind, c->stream);
-        if (e == cudaSuccess) {
-            if (want64)
-                convert_nodes<<<1024, 256, 0, c->stream>>>((const float *)tmp, (double *)c->d_grid, nval);
-            else
-                convert_nodes<<<1024, 256, 0, c->stream>>>((const double *)tmp, (float *)c->d_grid, nval);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(c->stream);
-        cudaFree(tmp);
-        if (e != cudaSuccess)
-            return fail(GC_ERR_CUDA, "gc_field_load: %s", cudaGetErrorString(e));
+    TRY(upload_nodes(c, g, data, data_on_device, &c->d_grid));
+    if (c->d_grid1) {
+        cudaFree(c->d_grid1);
+        c->d_grid1 = nullptr;
     }
+    c->gh.nodes1 = nullptr;
+    for (int &nb : c->blocks_per_sm) nb = 0;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->grid = *g;
     c->gh.nodes = c->d_grid;
@@ -860,6 +878,32 @@ int gc_field_load(gc_ctx *c, const gc_grid_desc *g, const void *data, int data_o
     c->gh.dth = kPi / (double)(g->n_th - 1);
     c->gh.dph = 2.0 * kPi / (double)g->n_ph;
     c->has_field = true;
+    return GC_OK;
+}
+
+int gc_field_load_next(gc_ctx *c, const void *data, int data_on_device, double t0_s, double t1_s)
+{
+    if (!c || !data)
+        return fail(GC_ERR_INVALID, "gc_field_load_next: null argument");
+    if (!c->has_field)
+        return fail(GC_ERR_STATE, "gc_field_load_next: load the first snapshot with gc_field_load first");
+    if (!(t1_s > t0_s) || !std::isfinite(t0_s) || !std::isfinite(t1_s))
+        return fail(GC_ERR_INVALID, "gc_field_load_next: need finite t0 < t1");
+    if (c->field_source != GC_FIELD_GRID)
+        return fail(GC_ERR_UNSUPPORTED, "gc_field_load_next: time-dependent fields run with GC_FIELD_GRID");
+    TRY(set_device(c));
+    drop_graphs(c);
+    if (c->d_grid1) {
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_grid1);
+        c->d_grid1 = nullptr;
+        c->gh.nodes1 = nullptr;
+    }
+    TRY(upload_nodes(c, &c->grid, data, data_on_device, &c->d_grid1));
+    c->gh.nodes1 = c->d_grid1;
+    c->gh.t_snap0 = t0_s;
+    c->gh.t_snap1 = t1_s;
+    for (int &nb : c->blocks_per_sm) nb = 0;
     return GC_OK;
 }
 
@@ -1527,6 +1571,8 @@ int gc_field_select(gc_ctx *c, int source)
         return fail(GC_ERR_INVALID, "gc_field_select: unknown source %d", source);
     if (source == GC_FIELD_SIREN) TRY(nn_ready(c, "gc_field_select"));
     if (source != GC_FIELD_GRID) {
+        if (c->gh.nodes1)
+            return fail(GC_ERR_UNSUPPORTED, "gc_field_select: time-dependent fields run with GC_FIELD_GRID");
         if (c->opt.precision != GC_PREC_FP32_MIXED)
             return fail(GC_ERR_UNSUPPORTED, "gc_field_select: the split-step push runs with GC_PREC_FP32_MIXED only");
         if (!c->has_field) return fail(GC_ERR_STATE, "gc_field_select: load the grid first");

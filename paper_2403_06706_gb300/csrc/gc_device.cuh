@@ -124,6 +124,11 @@ struct GridMeta {
     const T *nodes;   // [n_ph][n_th][n_r][8]
     int n_r, n_th, n_ph, ideal;
     T r_min, inv_dr, inv_dth, inv_dph;
+    // time-dependent fields: a second snapshot span seconds after the first (null: steady),
+    // the first snapshot's time (s)
+    const T *nodes1;
+    T span, inv_span;
+    double t_snap0;
 };
 
 // Interpolated field at one point.
@@ -136,6 +141,7 @@ struct Sample {
     T dB[3][3], dE[3][3];
     T g[3][3];
     T dPhi[3]; // derivatives of the potential channel (two-fluid fields only), like dB[d]
+    T dBdt[3], dEdt[3]; // time derivatives (time-dependent fields only)
     uint32_t flags;
 };
 
@@ -379,6 +385,38 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     s.flags = flags;
 }
 
+// Time-dependent fields: both snapshots gathered at the point, every quantity blended
+// linearly at t_rel seconds after the first snapshot (held constant outside the window),
+// and the time derivatives taken as the snapshots' secant slope inside it.
+template <typename T>
+__device__ __forceinline__ void gather_td(const GridMeta<T> &gm, T x, T y, T z, T t_rel, Sample<T> &s)
+{
+    gather(gm, x, y, z, s);
+    GridMeta<T> g1 = gm;
+    g1.nodes = gm.nodes1;
+    Sample<T> s1;
+    gather(g1, x, y, z, s1);
+    // the window test on the time itself: at t_rel == span the weight may round above 1
+    const bool inside = (t_rel >= T(0)) && (t_rel <= gm.span);
+    T w = t_rel * gm.inv_span;
+    w = w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
+    const T rate = inside ? gm.inv_span : T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s.dBdt[c] = (s1.B[c] - s.B[c]) * rate;
+        s.dEdt[c] = (s1.E[c] - s.E[c]) * rate;
+        s.B[c] += w * (s1.B[c] - s.B[c]);
+        s.E[c] += w * (s1.E[c] - s.E[c]);
+        s.dPhi[c] += w * (s1.dPhi[c] - s.dPhi[c]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            s.dB[d][c] += w * (s1.dB[d][c] - s.dB[d][c]);
+            s.dE[d][c] += w * (s1.dE[d][c] - s.dE[d][c]);
+        }
+    }
+    s.flags |= s1.flags;
+}
+
 // ----------------------------------------------------------------------------------------
 // Relativistic guiding-centre right-hand side, Eqs. 1-2 (Eq. 3: mu_B constant).
 template <typename T>
@@ -420,7 +458,7 @@ __device__ __forceinline__ void jvec(const T dF[3][3], const T p[3], T out[3])
         out[c] = dF[0][c] * p[0] + dF[1][c] * p[1] + dF[2][c] * p[2];
 }
 
-template <typename T>
+template <typename T, bool TD = false>
 __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int ideal, T u, T mub,
                                     T F[4], Aux<T> &aux)
 {
@@ -514,6 +552,21 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             br[c] = c_gB * gB[c] + c_vE * vE[c] + v2 * kap[c] + vpar * (vgb[c] + bgv[c]) + vgv[c];
+        // time-dependent fields: v_par db/dt + dv_E/dt in the bracket, and db/dt in Eq. 2's
+        // v_E product, with db/dt = (dB/dt - b (b.dB/dt)) / B and
+        // dv_E/dt = (dE/dt x B + E x dB/dt) / B^2 - 2 v_E (b.dB/dt) / B
+        T dbdt[3] = {T(0), T(0), T(0)};
+        if constexpr (TD) {
+            const T bdB = dot3(b, s.dBdt);
+            T e1[3], e2[3];
+            cross3(s.dEdt, s.B, e1);
+            cross3(s.E, s.dBdt, e2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dbdt[c] = (s.dBdt[c] - b[c] * bdB) * inv_B;
+                br[c] += vpar * dbdt[c] + (e1[c] + e2[c]) * inv_B2 - T(2) * vE[c] * bdB * inv_B;
+            }
+        }
         T bxbr[3];
         cross3(b, br, bxbr);
         const T pre = gamma * inv_B * ph.inv_qm;
@@ -524,7 +577,7 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         T w[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            w[c] = vpar * kap[c] + vgb[c];
+            w[c] = vpar * kap[c] + vgb[c] + dbdt[c];
         F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB + gamma * dot3(vE, w);
     }
     aux.gamma = gamma;
@@ -535,13 +588,16 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         aux.b[c] = b[c];
 }
 
-template <typename T>
+template <typename T, bool TD = false>
 __device__ __forceinline__ uint32_t eval_F(const GridMeta<T> &gm, const Phys<T> &ph, T x, T y, T z,
-                                           T u, T mub, T F[4], Aux<T> &aux)
+                                           T u, T mub, T F[4], Aux<T> &aux, T t_rel = T(0))
 {
     Sample<T> s;
-    gather(gm, x, y, z, s);
-    rhs(s, ph, gm.ideal, u, mub, F, aux);
+    if constexpr (TD)
+        gather_td(gm, x, y, z, t_rel, s);
+    else
+        gather(gm, x, y, z, s);
+    rhs<T, TD>(s, ph, gm.ideal, u, mub, F, aux);
     return s.flags;
 }
 

@@ -101,6 +101,9 @@ struct GridHost {
     const void *nodes;
     int n_r, n_th, n_ph, ideal, is_f64;
     double r_min, dr, dth, dph;
+    // time-dependent fields: a second snapshot (null: steady) and the snapshot times (s)
+    const void *nodes1;
+    double t_snap0, t_snap1;
 };
 struct PhysHost {
     double qm, inv_m, inv_c2;
@@ -110,7 +113,7 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
                         int block, int grid, cudaStream_t s);
 cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
                           const InjectParams &p, cudaStream_t s);
-int push_max_blocks_per_sm(int precision, int block);
+int push_max_blocks_per_sm(int precision, int block, bool time_dependent = false);
 // one split-step kernel (FP32 path)
 cudaError_t launch_split(int kind, const PhysHost &ph, const SplitParams &p, cudaStream_t s);
 // grid field samples (FP32 grid) at R (cap x 3, m; count on the device or cap)

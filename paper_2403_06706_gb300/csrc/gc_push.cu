@@ -493,8 +493,8 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
 // ----------------------------------------------------------------------------------------
 // Fused push: one thread owns a particle for all the steps of a launch and evaluates the
 // grid field inline (one copy of the evaluation serves all phases: instruction cache).
-template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
+template <typename T, bool TD = false>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? 3 : 4) : 2) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                    const PushParams P)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -509,6 +509,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
     // Eq. 5-6 weights at tau = 1: 3/2, -1/2 (AB2) and 2/3, 5/12, -1/12 (AM3)
     const StepW<T> w1 = {dtT * T(1.5), dtT * T(-0.5), dtT * T(2.0 / 3.0), dtT * T(5.0 / 12.0),
                          dtT * T(-1.0 / 12.0)};
+    // time-dependent fields: time of the call's start after the first snapshot
+    const T tr0 = TD ? (T)(t0 - gm.t_snap0) : T(0);
 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.st.n; i += stride) {
         PConst c;
@@ -522,6 +524,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
 
         for (int k = 0; k < P.n_steps; ++k) {
             const StepW<T> w = step_weights(w1, dtT, s.hprev);
+            // the predictor, corrector and restart evaluations are at the step's end time,
+            // the start-up's F^{n-1} one step earlier
+            const T t_end = TD ? tr0 + (T)(P.kbase + k + 1) * dtT : T(0);
             int n_phase = 2;
 #pragma unroll 1
             for (int phase = 0; phase < n_phase; ++phase) {
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) push_kernel(const
                 phase_point(phase, s, w, dtT, px, py, pz, pu);
                 T Fo[4];
                 Aux<T> ax;
-                s.flags |= eval_F(gm, ph, px, py, pz, pu, s.mub, Fo, ax);
+                s.flags |= eval_F<T, TD>(gm, ph, px, py, pz, pu, s.mub, Fo, ax, phase == 3 ? t_end - dtT : t_end);
                 phase_consume(phase, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, t0, (long long)(P.kbase + k + 1),
                               n_coll, n_reb);
             }
@@ -582,7 +587,7 @@ __device__ __forceinline__ InjDraw inj_draw(const EnsDev &E, uint32_t id, uint32
     return d;
 }
 
-template <typename T>
+template <typename T, bool TD = false>
 __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                      const InjectParams P)
 {
@@ -599,7 +604,10 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
     const double mu0 = d.mu0, pm = d.pm;
     const uint4 w0 = d.w0;
     Sample<T> s;
-    gather(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], s);
+    if constexpr (TD)
+        gather_td(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], (T)(P.t - gm.t_snap0), s);
+    else
+        gather(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], s);
     const double Bm = (double)m_sqrt(dot3(s.B, s.B));
     const double u = mu0 * pm;
     const double mub = (1.0 - mu0 * mu0) * pm * pm * P.m / (2.0 * Bm);
@@ -608,9 +616,10 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
     const T x = (T)E.R0[0], y = (T)E.R0[1], z = (T)E.R0[2], uT = (T)u, mubT = (T)mub;
     const T dt = (T)P.dt_init;
     uint32_t flags = s.flags;
-    flags |= eval_F(gm, ph, x, y, z, uT, mubT, F0, a0x);
-    flags |= eval_F(gm, ph, x - dt * F0[0], y - dt * F0[1], z - dt * F0[2], uT - dt * F0[3], mubT,
-                    F1, a1x);
+    const T t_inj = TD ? (T)(P.t - gm.t_snap0) : T(0);
+    flags |= eval_F<T, TD>(gm, ph, x, y, z, uT, mubT, F0, a0x, t_inj);
+    flags |= eval_F<T, TD>(gm, ph, x - dt * F0[0], y - dt * F0[1], z - dt * F0[2], uT - dt * F0[3], mubT,
+                           F1, a1x, t_inj - dt);
     const int64_t cap = P.st.cap;
     P.st.x[i] = E.R0[0];
     P.st.y[i] = E.R0[1];
@@ -850,6 +859,10 @@ static GridMeta<T> make_meta(const GridHost &g)
     m.inv_dr = (T)(1.0 / g.dr);
     m.inv_dth = (T)(1.0 / g.dth);
     m.inv_dph = (T)(1.0 / g.dph);
+    m.nodes1 = static_cast<const T *>(g.nodes1);
+    m.span = g.nodes1 ? (T)(g.t_snap1 - g.t_snap0) : T(1);
+    m.inv_span = g.nodes1 ? (T)(1.0 / (g.t_snap1 - g.t_snap0)) : T(0);
+    m.t_snap0 = g.t_snap0;
     return m;
 }
 
@@ -870,10 +883,18 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
                         int block, int grid, cudaStream_t s)
 {
     cudaGetLastError(); // report this launch only
-    if (precision == 0)
-        push_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
-    else
-        push_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+    const bool td = g.nodes1 != nullptr;
+    if (precision == 0) {
+        if (td)
+            push_kernel<double, true><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+        else
+            push_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+    } else {
+        if (td)
+            push_kernel<float, true><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+        else
+            push_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+    }
     return cudaGetLastError();
 }
 
@@ -884,10 +905,18 @@ cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
     const int grid = (int)((p.count + block - 1) / block);
     if (grid == 0)
         return cudaSuccess;
-    if (precision == 0)
-        inject_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
-    else
-        inject_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+    const bool td = g.nodes1 != nullptr;
+    if (precision == 0) {
+        if (td)
+            inject_kernel<double, true><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+        else
+            inject_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+    } else {
+        if (td)
+            inject_kernel<float, true><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+        else
+            inject_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+    }
     return cudaGetLastError();
 }
 
@@ -931,16 +960,25 @@ cudaError_t preload_kernels()
     cudaFuncAttributes a;
     cudaError_t e = cudaFuncGetAttributes(&a, push_kernel<float>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<double>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<float, true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<double, true>);
     return e;
 }
 
-int push_max_blocks_per_sm(int precision, int block)
+int push_max_blocks_per_sm(int precision, int block, bool time_dependent)
 {
     int nb = 0;
-    if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<double>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<float>, block, 0);
+    if (precision == 0) {
+        if (time_dependent)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<double, true>, block, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<double>, block, 0);
+    } else {
+        if (time_dependent)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<float, true>, block, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<float>, block, 0);
+    }
     return nb;
 }
 

@@ -156,7 +156,7 @@ EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_part
            "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc",
            "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn", "gc_gemm_bf16", "gc_siren_set", "gc_siren_get",
            "gc_siren_eval", "gc_siren_field", "gc_field_targets", "gc_siren_loss_grad", "gc_field_fit",
-           "gc_field_select")
+           "gc_field_select", "gc_field_load_next")
 
 _lib = None
 
@@ -177,6 +177,7 @@ def load(path: str | None = None):
         "gc_destroy": (None, [vp]),
         "gc_last_error": (C.c_char_p, []),
         "gc_field_load": (C.c_int, [vp, C.POINTER(GridDesc), vp, C.c_int]),
+        "gc_field_load_next": (C.c_int, [vp, vp, C.c_int, C.c_double, C.c_double]),
         "gc_particles_inject": (C.c_int, [vp, C.POINTER(EnsembleDesc), C.c_int]),
         "gc_advance": (C.c_int, [vp, C.c_double, C.c_int64, C.c_double]),
         "gc_tally": (C.c_int, [vp, C.POINTER(TallyDesc), C.POINTER(TallyOut)]),
@@ -283,8 +284,8 @@ class Context:
 
     # field -------------------------------------------------------------------
     def field_load(self, nodes, r_min_au: float, r_max_au: float, ideal=True):
-        """ideal: True (E_par = 0), False (E_par = E.b) or 2 (two-fluid: E_par = -b.grad(Phi))."""
-        """nodes: [n_ph][n_th][n_r][8] float32/float64, numpy (host) or torch CUDA tensor."""
+        """nodes: [n_ph][n_th][n_r][8] float32/float64, numpy (host) or torch CUDA tensor.
+        ideal: True (E_par = 0), False (E_par = E.b) or 2 (two-fluid: E_par = -b.grad(Phi))."""
         g = GridDesc()
         on_dev = 0
         if hasattr(nodes, "is_cuda"):  # torch tensor
@@ -304,6 +305,26 @@ class Context:
         g.ideal = 2 if ideal == 2 else (1 if ideal else 0)
         _check(load().gc_field_load(self._h, C.byref(g), ptr, on_dev), "gc_field_load")
         self._grid_keep = nodes
+        self._grid_shape = (g.n_ph, g.n_th, g.n_r, 8, g.dtype)
+
+    def field_load_next(self, nodes, t0_s: float, t1_s: float):
+        """Second snapshot of the loaded field (same shape and dtype), the two at times t0_s and
+        t1_s: the field becomes linear in time between them and holds the nearer one outside."""
+        if hasattr(nodes, "is_cuda"):
+            assert nodes.is_contiguous()
+            dt = DTYPE_F64 if str(nodes.dtype) == "torch.float64" else DTYPE_F32
+            shape = tuple(int(v) for v in nodes.shape) + (dt,)
+            ptr, on_dev = C.c_void_p(nodes.data_ptr()), (1 if nodes.is_cuda else 0)
+        else:
+            nodes = np.ascontiguousarray(nodes)
+            dt = DTYPE_F64 if nodes.dtype == np.float64 else DTYPE_F32
+            shape = tuple(nodes.shape) + (dt,)
+            ptr, on_dev = C.c_void_p(nodes.ctypes.data), 0
+        if shape != getattr(self, "_grid_shape", None):
+            raise ValueError("field_load_next: snapshot %s does not match the loaded grid %s"
+                             % (shape, getattr(self, "_grid_shape", None)))
+        _check(load().gc_field_load_next(self._h, ptr, on_dev, float(t0_s), float(t1_s)), "gc_field_load_next")
+        self._grid_keep1 = nodes
 
     # particles ---------------------------------------------------------------
     def inject(self, ensembles):

@@ -23,11 +23,14 @@ def oracle_ensembles(ens):
 
 
 def run_gpu(nodes, wind, ens, calls, precision, seed=0, tally=None, dt_init=None, launch=None,
-            ideal=True, **opt):
-    """calls: list of (dt, n_steps, lambda_au). Returns (state, tallies, stats)."""
+            ideal=True, nodes1=None, t_snap=None, **opt):
+    """calls: list of (dt, n_steps, lambda_au); nodes1, t_snap: a second snapshot and the
+    (t0, t1) window of a time-dependent field. Returns (state, tallies, stats)."""
     dt0 = dt_init if dt_init is not None else calls[0][0]
     with gcpush.Context(precision=precision, device=0, seed=seed, dt_init=dt0, **opt) as ctx:
         ctx.field_load(nodes, wind.r_min_au, wind.r_max_au, ideal=ideal)
+        if nodes1 is not None:
+            ctx.field_load_next(nodes1, *t_snap)
         ctx.inject(ens)
         if launch:
             ctx.set_launch(**launch)
@@ -52,14 +55,24 @@ def tally_spec(t: dict) -> oracle.TallySpec:
 
 
 def run_oracle(nodes, wind, ens, calls, seed=0, tally=None, dt_init=None, subset=None,
-               n_threads=0, ideal=True, **opt):
-    f = oracle.grid_field(nodes, wind.r_min_au * AU, wind.r_max_au * AU, ideal=ideal)
+               n_threads=0, ideal=True, nodes1=None, t_snap=None, perturb=None, **opt):
+    """perturb: (direction seed, eps) scales R and gamma v_par after injection by
+    1 + eps * (a seeded standard normal per particle and component)."""
+    if nodes1 is None:
+        f = oracle.grid_field(nodes, wind.r_min_au * AU, wind.r_max_au * AU, ideal=ideal)
+    else:
+        f = oracle.grid_field_pair(nodes, nodes1, t_snap[0], t_snap[1], wind.r_min_au * AU,
+                                   wind.r_max_au * AU, ideal=ideal)
     p = oracle.params(seed=seed, **opt)
     oe = oracle_ensembles(ens)
     dt0 = dt_init if dt_init is not None else calls[0][0]
     st = oracle.inject(f, p, oe, [e.count for e in ens], dt=dt0, n_threads=n_threads)
     if subset is not None:
         st = st.subset(subset)
+    if perturb is not None:
+        rng = np.random.default_rng(perturb[0])
+        for k in ("x", "y", "z", "u"):
+            st.arrays[k] *= 1.0 + perturb[1] * rng.standard_normal(st.arrays[k].shape)
     T = oracle.TallyArrays(tally_spec(tally), len(ens)) if tally else None
     t, step = 0.0, 0
     stats = np.zeros(2, dtype=np.uint64)
@@ -103,3 +116,18 @@ def compare_states(g, o, tol, pm, skip=None, lam=None):
     ls = (0.01 * AU) if lam is None else lam[keep]
     out["s_rem"] = np.max(np.abs(g["s_rem"][keep] - o["s_rem"][keep]) / ls)
     return out
+
+
+def ill_conditioned(nodes, wind, ens, calls, final, pm, eps=3e-7, n_dir=2, **kw):
+    """Particles whose FP64 oracle result is itself unstable at FP32 resolution: the oracle
+    rerun with the start state moved by +-eps (relative) along n_dir seeded directions ends
+    more than 1e-5 |p|/m away in gamma v_par from ``final`` (the unperturbed oracle run). A
+    trajectory that passes within about eps of a cell face is such a case: the trilinear
+    field's gradient jumps across the face, so the side a rounding puts the point on
+    changes the mirror force there (a tie between two correct values)."""
+    bad = np.zeros(final["u"].shape[0], dtype=bool)
+    for d in range(n_dir):
+        for sgn in (1.0, -1.0):
+            o, _, _ = run_oracle(nodes, wind, ens, calls, perturb=(1000 + d, sgn * eps), **kw)
+            bad |= np.abs(o["u"] - final["u"]) > 1e-5 * pm
+    return bad
