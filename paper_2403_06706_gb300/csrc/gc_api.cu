@@ -369,7 +369,8 @@ int push_grid(gc_ctx *c)
 {
     int &nb = c->blocks_per_sm[c->block / 32];
     if (nb <= 0) {
-        nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block, c->gh.nodes1 != nullptr);
+        nb = gcp::push_max_blocks_per_sm(c->opt.precision, c->block, c->gh.nodes1 != nullptr,
+                                        c->gh.ideal == 2);
         cudaGetLastError(); // an occupancy query failure only means "one block"
         if (nb < 1) nb = 1;
     }

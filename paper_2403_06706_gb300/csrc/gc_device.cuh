@@ -17,6 +17,11 @@ namespace gcp {
 
 enum : uint32_t { FLAG_OUT_OF_GRID = 1u, FLAG_AXIS = 2u, FLAG_NONFINITE = 4u };
 
+// Whether an evaluation uses the potential channel (two-fluid E_par, Sect. 2.2): decided at
+// compile time for the fused push (the grid's mode is known at launch), at run time from
+// GridMeta::ideal == 2 for the split-step kernels.
+enum : int { POT_NONE = 0, POT_ON = 1, POT_RUNTIME = -1 };
+
 // ----------------------------------------------------------------------------------------
 // Philox-4x32-10: ten rounds of two 32x32 -> 64 multiplies; the two key words are bumped
 // by the Weyl constants 0x9E3779B9 / 0xBB67AE85 before every round but the first.
@@ -160,6 +165,14 @@ __device__ __forceinline__ void load_node(const double *__restrict__ p, double v
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
 }
 
+// A whole FP32 node record (32 bytes, 32-byte aligned) in one 256-bit read-only load.
+__device__ __forceinline__ void load_node_pairs(const float *p, unsigned long long q[4])
+{
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(q[0]), "=l"(q[1]), "=l"(q[2]), "=l"(q[3])
+        : "l"(p));
+}
+
 // Two FP32 channels in one 64-bit register and the packed f32x2 arithmetic of sm_100+ (two
 // independent IEEE operations per instruction, the same results as two scalar ones).
 __device__ __forceinline__ unsigned long long p2_sub(unsigned long long a, unsigned long long b)
@@ -193,7 +206,7 @@ __device__ __forceinline__ void p2_split(unsigned long long v, float &lo, float 
 // the interpolant (Sect. 2.2). Node-centred grid, poles included in theta, periodic in phi.
 // Positions more than one radial cell outside the grid are flagged; beyond the edge nodes
 // the interpolant is extended as a constant.
-template <typename T>
+template <typename T, int POT = POT_RUNTIME>
 __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sample<T> &s)
 {
     uint32_t flags = 0;
@@ -237,27 +250,27 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     const uint32_t o0 = (((uint32_t)k * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
     const uint32_t o1 = (((uint32_t)k1 * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
 
+    const bool use_pot = POT == POT_ON || (POT == POT_RUNTIME && gm.ideal == 2);
+    // FP32: each 32-byte node record in one 256-bit load, as four packed channel pairs
+    // (Bx By | Bz Ex | Ey Ez | |B| Phi), interpolated two channels at a time (the fourth
+    // pair for the potential's gradient only)
+    unsigned long long c2[2][2][2][4];
     if constexpr (sizeof(T) == 4) {
-        // FP32: the six channels as three packed pairs (Bx By | Bz Ex | Ey Ez), loaded as
-        // 16 + 8 bytes of each 32-byte node record and interpolated two at a time
-        unsigned long long c2[2][2][2][3];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
                 const float *p = (const float *)gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
 #pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(p + 8 * a));
-                    c2[b][cc][a][0] = q.x;
-                    c2[b][cc][a][1] = q.y;
-                    c2[b][cc][a][2] = __ldg(reinterpret_cast<const unsigned long long *>(p + 8 * a + 4));
-                }
+                for (int a = 0; a < 2; ++a)
+                    load_node_pairs(p + 8 * a, c2[b][cc][a]);
             }
         }
         const unsigned long long FR = p2_bcast((float)fr), FT = p2_bcast((float)ft), FP = p2_bcast((float)fp);
 #pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
+        for (int pr = 0; pr < 4; ++pr) {
+            if (pr == 3 && !use_pot)
+                break;
             unsigned long long L[2][2], D[2][2];
 #pragma unroll
             for (int b = 0; b < 2; ++b)
@@ -286,7 +299,11 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int ch = 2 * pr + h;
-                if (ch < 3) {
+                if (ch == 6) {
+                    // |B|: not used
+                } else if (ch == 7) {
+                    s.dPhi[0] = rr[h]; s.dPhi[1] = tt[h]; s.dPhi[2] = pp[h];
+                } else if (ch < 3) {
                     s.B[ch] = vv[h]; s.dB[0][ch] = rr[h]; s.dB[1][ch] = tt[h]; s.dB[2][ch] = pp[h];
                 } else {
                     s.E[ch - 3] = vv[h]; s.dE[0][ch - 3] = rr[h]; s.dE[1][ch - 3] = tt[h]; s.dE[2][ch - 3] = pp[h];
@@ -340,17 +357,17 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     }
     }
 
-    // two-fluid fields: the potential channel's index-space gradient (its value is not used)
-    if (gm.ideal == 2) {
+    // two-fluid fields: the potential channel's index-space gradient (its value is not
+    // used; the FP32 branch above takes it from the fourth pairs)
+    if (sizeof(T) == 8 && use_pot) {
         T ph[2][2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                const T *p = gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u) + 7;
-                ph[b][cc][0] = __ldg(p);
-                ph[b][cc][1] = __ldg(p + 8);
-            }
+            for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+                    ph[b][cc][a] = __ldg(gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u) + 8 * a + 7);
         T L[2][2], D[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b)
@@ -369,7 +386,7 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
         s.dPhi[0] = Dr[0] + fp * (Dr[1] - Dr[0]);
         s.dPhi[1] = Dt[0] + fp * (Dt[1] - Dt[0]);
         s.dPhi[2] = V[1] - V[0];
-    } else {
+    } else if (!use_pot) {
         s.dPhi[0] = s.dPhi[1] = s.dPhi[2] = T(0);
     }
 
@@ -388,14 +405,14 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
 // Time-dependent fields: both snapshots gathered at the point, every quantity blended
 // linearly at t_rel seconds after the first snapshot (held constant outside the window),
 // and the time derivatives taken as the snapshots' secant slope inside it.
-template <typename T>
+template <typename T, int POT = POT_RUNTIME>
 __device__ __forceinline__ void gather_td(const GridMeta<T> &gm, T x, T y, T z, T t_rel, Sample<T> &s)
 {
-    gather(gm, x, y, z, s);
+    gather<T, POT>(gm, x, y, z, s);
     GridMeta<T> g1 = gm;
     g1.nodes = gm.nodes1;
     Sample<T> s1;
-    gather(g1, x, y, z, s1);
+    gather<T, POT>(g1, x, y, z, s1);
     // the window test on the time itself: at t_rel == span the weight may round above 1
     const bool inside = (t_rel >= T(0)) && (t_rel <= gm.span);
     T w = t_rel * gm.inv_span;
@@ -458,7 +475,7 @@ __device__ __forceinline__ void jvec(const T dF[3][3], const T p[3], T out[3])
         out[c] = dF[0][c] * p[0] + dF[1][c] * p[1] + dF[2][c] * p[2];
 }
 
-template <typename T, bool TD = false>
+template <typename T, bool TD = false, int POT = POT_RUNTIME>
 __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int ideal, T u, T mub,
                                     T F[4], Aux<T> &aux)
 {
@@ -529,9 +546,11 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 
     // ideal 1: E_par = 0 (ideal Ohm's law); 0: the interpolated E.b; 2: the two-fluid
     // correction -grad(Phi) (Sect. 2.2): E_par = -b.grad(Phi) = -sum_d dPhi/di_d (g_d . b)
-    const T Epar = ideal == 1 ? T(0)
-                              : (ideal == 2 ? -(s.dPhi[0] * pb[0] + s.dPhi[1] * pb[1] + s.dPhi[2] * pb[2])
-                                            : dot3(s.E, b));
+    T Epar;
+    if (POT == POT_ON || (POT == POT_RUNTIME && ideal == 2))
+        Epar = -(s.dPhi[0] * pb[0] + s.dPhi[1] * pb[1] + s.dPhi[2] * pb[2]);
+    else
+        Epar = ideal ? T(0) : dot3(s.E, b);
     // gamma^2 = 1 + (gamma v)^2 / c^2 with (gamma v)^2 = u^2 + 2 mu_B B / m
     const T g2 = T(1) + (u * u + T(2) * mub * Bm * ph.inv_m) * ph.inv_c2;
     const T inv_g = m_rsqrt(g2);
@@ -588,16 +607,16 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         aux.b[c] = b[c];
 }
 
-template <typename T, bool TD = false>
+template <typename T, bool TD = false, int POT = POT_RUNTIME>
 __device__ __forceinline__ uint32_t eval_F(const GridMeta<T> &gm, const Phys<T> &ph, T x, T y, T z,
                                            T u, T mub, T F[4], Aux<T> &aux, T t_rel = T(0))
 {
     Sample<T> s;
     if constexpr (TD)
-        gather_td(gm, x, y, z, t_rel, s);
+        gather_td<T, POT>(gm, x, y, z, t_rel, s);
     else
-        gather(gm, x, y, z, s);
-    rhs<T, TD>(s, ph, gm.ideal, u, mub, F, aux);
+        gather<T, POT>(gm, x, y, z, s);
+    rhs<T, TD, POT>(s, ph, gm.ideal, u, mub, F, aux);
     return s.flags;
 }
 

@@ -113,7 +113,7 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
                         int block, int grid, cudaStream_t s);
 cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
                           const InjectParams &p, cudaStream_t s);
-int push_max_blocks_per_sm(int precision, int block, bool time_dependent = false);
+int push_max_blocks_per_sm(int precision, int block, bool time_dependent = false, bool potential = false);
 // one split-step kernel (FP32 path)
 cudaError_t launch_split(int kind, const PhysHost &ph, const SplitParams &p, cudaStream_t s);
 // grid field samples (FP32 grid) at R (cap x 3, m; count on the device or cap)

@@ -491,10 +491,18 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
     }
 }
 // ----------------------------------------------------------------------------------------
+// Resident CTAs of 128 threads per SM the FP32 push is compiled for (register budget:
+// 65536 / (128 x blocks) per thread); the time-dependent variant carries more state.
+#ifndef GC_PUSH_F32_MIN_BLOCKS
+#define GC_PUSH_F32_MIN_BLOCKS 4
+#endif
+constexpr int kMinBlocksF32 = GC_PUSH_F32_MIN_BLOCKS;
+constexpr int kMinBlocksF32TD = 3;
+
 // Fused push: one thread owns a particle for all the steps of a launch and evaluates the
 // grid field inline (one copy of the evaluation serves all phases: instruction cache).
-template <typename T, bool TD = false>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? 3 : 4) : 2) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
+template <typename T, bool TD, int POT>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : kMinBlocksF32) : 2) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                    const PushParams P)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -534,7 +542,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? 3 : 4) : 2) push_k
                 phase_point(phase, s, w, dtT, px, py, pz, pu);
                 T Fo[4];
                 Aux<T> ax;
-                s.flags |= eval_F<T, TD>(gm, ph, px, py, pz, pu, s.mub, Fo, ax, phase == 3 ? t_end - dtT : t_end);
+                s.flags |= eval_F<T, TD, POT>(gm, ph, px, py, pz, pu, s.mub, Fo, ax,
+                                              phase == 3 ? t_end - dtT : t_end);
                 phase_consume(phase, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, t0, (long long)(P.kbase + k + 1),
                               n_coll, n_reb);
             }
@@ -587,7 +596,7 @@ __device__ __forceinline__ InjDraw inj_draw(const EnsDev &E, uint32_t id, uint32
     return d;
 }
 
-template <typename T, bool TD = false>
+template <typename T, bool TD, int POT>
 __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                      const InjectParams P)
 {
@@ -605,9 +614,9 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
     const uint4 w0 = d.w0;
     Sample<T> s;
     if constexpr (TD)
-        gather_td(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], (T)(P.t - gm.t_snap0), s);
+        gather_td<T, POT>(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], (T)(P.t - gm.t_snap0), s);
     else
-        gather(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], s);
+        gather<T, POT>(gm, (T)E.R0[0], (T)E.R0[1], (T)E.R0[2], s);
     const double Bm = (double)m_sqrt(dot3(s.B, s.B));
     const double u = mu0 * pm;
     const double mub = (1.0 - mu0 * mu0) * pm * pm * P.m / (2.0 * Bm);
@@ -617,9 +626,9 @@ __global__ void __launch_bounds__(256) inject_kernel(const GridMeta<T> gm, const
     const T dt = (T)P.dt_init;
     uint32_t flags = s.flags;
     const T t_inj = TD ? (T)(P.t - gm.t_snap0) : T(0);
-    flags |= eval_F<T, TD>(gm, ph, x, y, z, uT, mubT, F0, a0x, t_inj);
-    flags |= eval_F<T, TD>(gm, ph, x - dt * F0[0], y - dt * F0[1], z - dt * F0[2], uT - dt * F0[3], mubT,
-                           F1, a1x, t_inj - dt);
+    flags |= eval_F<T, TD, POT>(gm, ph, x, y, z, uT, mubT, F0, a0x, t_inj);
+    flags |= eval_F<T, TD, POT>(gm, ph, x - dt * F0[0], y - dt * F0[1], z - dt * F0[2], uT - dt * F0[3],
+                                mubT, F1, a1x, t_inj - dt);
     const int64_t cap = P.st.cap;
     P.st.x[i] = E.R0[0];
     P.st.y[i] = E.R0[1];
@@ -879,22 +888,38 @@ static Phys<T> make_phys(const PhysHost &p)
     return q;
 }
 
+// The fused push and injection come in one variant per field mode: steady or time
+// dependent (two snapshots), with or without the potential channel (two-fluid E_par).
+template <typename T>
+using PushFn = void (*)(const GridMeta<T>, const Phys<T>, const PushParams);
+template <typename T>
+using InjectFn = void (*)(const GridMeta<T>, const Phys<T>, const InjectParams);
+
+template <typename T>
+PushFn<T> push_fn(bool td, bool pot)
+{
+    if (td)
+        return pot ? push_kernel<T, true, POT_ON> : push_kernel<T, true, POT_NONE>;
+    return pot ? push_kernel<T, false, POT_ON> : push_kernel<T, false, POT_NONE>;
+}
+
+template <typename T>
+InjectFn<T> inject_fn(bool td, bool pot)
+{
+    if (td)
+        return pot ? inject_kernel<T, true, POT_ON> : inject_kernel<T, true, POT_NONE>;
+    return pot ? inject_kernel<T, false, POT_ON> : inject_kernel<T, false, POT_NONE>;
+}
+
 cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, const PushParams &p,
                         int block, int grid, cudaStream_t s)
 {
     cudaGetLastError(); // report this launch only
-    const bool td = g.nodes1 != nullptr;
-    if (precision == 0) {
-        if (td)
-            push_kernel<double, true><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
-        else
-            push_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
-    } else {
-        if (td)
-            push_kernel<float, true><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
-        else
-            push_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
-    }
+    const bool td = g.nodes1 != nullptr, pot = g.ideal == 2;
+    if (precision == 0)
+        push_fn<double>(td, pot)<<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+    else
+        push_fn<float>(td, pot)<<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
     return cudaGetLastError();
 }
 
@@ -905,18 +930,11 @@ cudaError_t launch_inject(int precision, const GridHost &g, const PhysHost &ph,
     const int grid = (int)((p.count + block - 1) / block);
     if (grid == 0)
         return cudaSuccess;
-    const bool td = g.nodes1 != nullptr;
-    if (precision == 0) {
-        if (td)
-            inject_kernel<double, true><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
-        else
-            inject_kernel<double><<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
-    } else {
-        if (td)
-            inject_kernel<float, true><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
-        else
-            inject_kernel<float><<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
-    }
+    const bool td = g.nodes1 != nullptr, pot = g.ideal == 2;
+    if (precision == 0)
+        inject_fn<double>(td, pot)<<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+    else
+        inject_fn<float>(td, pot)<<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
     return cudaGetLastError();
 }
 
@@ -958,27 +976,21 @@ cudaError_t launch_grid_samples(const GridHost &g, const float *R, int64_t cap, 
 cudaError_t preload_kernels()
 {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, push_kernel<float>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<double>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<float, true>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_kernel<double, true>);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+        e = cudaFuncGetAttributes(&a, push_fn<float>(v & 1, v & 2));
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_fn<double>(v & 1, v & 2));
+    }
     return e;
 }
 
-int push_max_blocks_per_sm(int precision, int block, bool time_dependent)
+int push_max_blocks_per_sm(int precision, int block, bool time_dependent, bool potential)
 {
     int nb = 0;
-    if (precision == 0) {
-        if (time_dependent)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<double, true>, block, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<double>, block, 0);
-    } else {
-        if (time_dependent)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<float, true>, block, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_kernel<float>, block, 0);
-    }
+    if (precision == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_fn<double>(time_dependent, potential), block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_fn<float>(time_dependent, potential), block, 0);
     return nb;
 }
 
