@@ -10,6 +10,8 @@ the FP64 decision margin is below FP32 resolution; such particles are counted an
 Tallies: FP64 equal up to a handful of bin-edge samples; FP32 compared by chi-square on
 their marginals.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -309,21 +311,28 @@ def test_two_fluid_field_matches_oracle(precision):
 WIND1 = synth.WindSpec(64, 32, 64, B1=4.2e-9, u_sw=5.0e5, eps=0.15, n_modes=4, seed=3)
 
 
-@pytest.mark.parametrize("precision,t_snap", [("fp64", (0.0, 150.0)), ("fp64", (-50.0, 100.25)),
-                                              ("fp32", (0.0, 150.0))])
-def test_time_dependent_field_matches_oracle(precision, t_snap):
+@pytest.mark.parametrize("precision,t_snap,ideal", [("fp64", (0.0, 150.0), True), ("fp64", (-50.0, 100.25), True),
+                                                    ("fp32", (0.0, 150.0), True), ("fp64", (0.0, 150.0), 2),
+                                                    ("fp32", (0.0, 150.0), 2)])
+def test_time_dependent_field_matches_oracle(precision, t_snap, ideal):
     """A field that changes in time (Sect. 2.2's GCA with its time-derivative terms): the
     Parker wind at t0 turning into a faster, stronger, perturbed wind at t1, linear in time.
     The second window ends inside the run (between step times), so that the field holds the
-    second snapshot and its time derivatives drop to zero there. Against the oracle's
-    two-snapshot field; the result must differ from the steady run's."""
+    second snapshot and its time derivatives drop to zero there. With ideal = 2 both
+    snapshots carry a two-fluid potential (500 V and 300 V at 1 AU) and E_par is the blended
+    gradient. Against the oracle's two-snapshot field; the result must differ from the
+    steady run's."""
     dtype = np.float64 if precision == "fp64" else np.float32
     prec = gcpush.PREC_FP64 if precision == "fp64" else gcpush.PREC_FP32_MIXED
-    n0 = synth.wind_grid(WIND, dtype=dtype)
-    n1 = synth.wind_grid(WIND1, dtype=dtype)
+    w0, w1 = WIND, WIND1
+    if ideal == 2:
+        w0 = dataclasses.replace(WIND, phi1_v=500.0)
+        w1 = dataclasses.replace(WIND1, phi1_v=300.0)
+    n0 = synth.wind_grid(w0, dtype=dtype)
+    n1 = synth.wind_grid(w1, dtype=dtype)
     calls = [(0.5, 150, 0.0), (0.5, 150, 0.0)]
-    g, _, gs = run_gpu(n0, WIND, ENS, calls, prec, seed=23, nodes1=n1, t_snap=t_snap)
-    o, _, os_ = run_oracle(n0, WIND, ENS, calls, seed=23, nodes1=n1, t_snap=t_snap)
+    g, _, gs = run_gpu(n0, WIND, ENS, calls, prec, seed=23, nodes1=n1, t_snap=t_snap, ideal=ideal)
+    o, _, os_ = run_oracle(n0, WIND, ENS, calls, seed=23, nodes1=n1, t_snap=t_snap, ideal=ideal)
     pm = momentum_scale(o, n0, WIND, ENS)
     if precision == "fp64":
         _ints_equal(g, o)
@@ -336,13 +345,14 @@ def test_time_dependent_field_matches_oracle(precision, t_snap):
         # cell face met within rounding, where the trilinear gradient jumps) are counted and
         # bounded, and excused from the 1e-4 bound
         div = (g["ncoll"] != o["ncoll"]) | (g["event"] != o["event"]) | (g["t_birth"] != o["t_birth"])
-        ill = ill_conditioned(n0, WIND, ENS, calls, o, pm, seed=23, nodes1=n1, t_snap=t_snap)
+        ill = ill_conditioned(n0, WIND, ENS, calls, o, pm, seed=23, nodes1=n1, t_snap=t_snap, ideal=ideal)
         print("diverged", int(div.sum()), "ill-conditioned", np.flatnonzero(ill))
         assert div.mean() <= 0.02 and ill.mean() <= 0.01 and os_[0] > 100
-        err = compare_states(g, o.arrays, 1e-4, pm, skip=div | ill)
+        lam = np.array([e.lam_au for e in ENS])[o["ens"].astype(int)] * AU
+        err = compare_states(g, o.arrays, 1e-4, pm, skip=div | ill, lam=lam)
         for k, v in err.items():
             assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
-    gs0, _, _ = run_gpu(n0, WIND, ENS, calls, prec, seed=23)
+    gs0, _, _ = run_gpu(n0, WIND, ENS, calls, prec, seed=23, ideal=ideal)
     R = np.stack([g["x"], g["y"], g["z"]])
     R0 = np.stack([gs0["x"], gs0["y"], gs0["z"]])
     assert np.max(np.linalg.norm(R - R0, axis=0) / np.linalg.norm(R0, axis=0)) > 1e-6
