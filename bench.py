@@ -295,6 +295,87 @@ def _measured_peaks() -> dict:
         return {}
 
 
+def _max_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def e2e_sharded(args, wl, nodes, local, rank, n_rank, world, dist, pinned, k_steps):
+    """End-to-end throughput through the public API with the rank's particles split over
+    args.e2e_shards contexts, each on its own stream and driven by its own host thread:
+    every step each shard copies its state in from pinned host memory (gc_particles_set),
+    advances PUSH_STEPS steps (gc_advance) and copies its state and tallies out
+    (gc_particles_get, gc_tally). The library releases the GIL in every call, so one
+    shard's copies run while the others push."""
+    import threading
+
+    import torch
+
+    from paper_2403_06706_gb300 import gcpush, shard
+
+    K = max(1, args.e2e_shards)
+    ctxs, hosts, tally_bytes = [], [], 0
+    first = shard.id_base(rank, n_rank)
+    for k in range(K):
+        ens = [dataclasses.replace(e, count=e.count // K + (1 if k < e.count % K else 0)) for e in wl.ensembles]
+        c = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=torch.cuda.Stream(),
+                           seed=wl.seed, dt_init=wl.dt, id_base=first)
+        first += sum(e.count for e in ens)
+        c.field_load(nodes, wl.wind.r_min_au, wl.wind.r_max_au)
+        c.inject(ens)
+        c.set_launch(**LAUNCH)
+        c.tally_arm(**TALLY)
+        c.advance(wl.dt, PUSH_STEPS)
+        h = gcpush.state_buffers(c.n, alloc=pinned)
+        c.get_state(out=h)
+        c.set_state(h)
+        tally_bytes += sum(v.nbytes for v in c.tally_read().values())
+        ctxs.append(c)
+        hosts.append(h)
+    assert sum(c.n for c in ctxs) == n_rank
+    start = threading.Barrier(K + 1)
+    errors = []
+
+    def work(k):
+        c, h = ctxs[k], hosts[k]
+        try:
+            start.wait()
+            for _ in range(k_steps):
+                c.set_state(h)
+                c.advance(wl.dt, PUSH_STEPS)
+                c.get_state(out=h)
+                c.tally_read()
+        except Exception as e:  # reported after the join
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(K)]
+    for t in threads:
+        t.start()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    start.wait()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    el = _max_over_ranks(time.perf_counter() - t0, dist)
+    if errors:
+        raise errors[0]
+    nb = sum(gcpush.state_nbytes(h) for h in hosts)
+    for c in ctxs:
+        c.close()
+    return {"value": world * n_rank * PUSH_STEPS * k_steps / el, "unit": UNIT,
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + tally_bytes, "steps": k_steps,
+            "contexts": K, "host_threads": K,
+            "api": "per context: gc_particles_set (pinned host) + gc_advance + gc_particles_get + gc_tally"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +385,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-shards", type=int, default=4,
+                    help="contexts (streams, host threads) the end-to-end population is split over")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-neural", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -391,10 +474,10 @@ def main():
         pinned = lambda shape, dt: torch.empty(shape, dtype={np.float64: torch.float64,
                                                               np.uint32: torch.int32}[dt],
                                                pin_memory=True).numpy().view(dt)
+        k_e2e = max(1, min(args.steps, 3))
+        # one context: copy in, advance, copy out, one call after the other
         host = gcpush.state_buffers(ctx.n, alloc=pinned)
         ctx.get_state(out=host)
-        tally_bytes = sum(v.nbytes for v in ctx.tally_read().values())
-        k_e2e = max(1, min(args.steps, 3))
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -404,16 +487,12 @@ def main():
             ctx.get_state(out=host)
             ctx.tally_read()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        nb = gcpush.state_nbytes(host)
-        e2e = {"value": world * n_rank * PUSH_STEPS * k_e2e / el, "unit": UNIT,
-               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + tally_bytes,
-               "steps": k_e2e,
-               "api": "gc_particles_set (pinned host) + gc_advance + gc_particles_get + gc_tally"}
+        el1 = _max_over_ranks(time.perf_counter() - t0, dist)
+        single = {"value": world * n_rank * PUSH_STEPS * k_e2e / el1, "unit": UNIT, "contexts": 1}
+        # the same population split over contexts on their own streams, one host thread each:
+        # one shard's copies overlap the others' pushes
+        e2e = e2e_sharded(args, wl, nodes, local, rank, n_rank, world, dist, pinned, k_e2e)
+        e2e["single_context"] = single
     ctx.close()
 
     # ---------------- plain FP64 path on the same workload ----------------------------
