@@ -20,6 +20,11 @@
 // The epilogue of half 0 overlaps the MMAs of half 1 (it may overwrite input features
 // 0-127 once half 1 has consumed them), and the epilogue of half 1 overlaps the next
 // layer's half-0 MMAs over input features 0-127 (the features half 0 has just written).
+// The output layer also runs in two K halves (input features 0-127 during the last
+// epilogue of half 1, then 128-255) into columns 0-31 of the drained half-0 accumulator,
+// and overlaps the next tile's first layer: its half 0 is written once the output MMAs over
+// features 0-127 are done, and the output accumulator is read before the next tile's MMAs
+// may start; the previous tile's outputs are stored while those MMAs run.
 //
 // Warp roles (576 threads): warps 0-15 compute; all of them work on one output half at a
 // time, warp w on features 32 (w % 4) + lane of the half (warp w may only touch
@@ -108,9 +113,72 @@ __device__ __forceinline__ bool wait_abort(uint64_t *bar, uint32_t parity, volat
     return false;
 }
 
+// Output rows of one tile from the output accumulator v (16 columns of this thread's row
+// pr): raw outputs y and J, or the physical field for the push.
+__device__ __forceinline__ void store_out(const EvalParams &p, const float (&b5)[8], const float (&v)[16],
+                                          int64_t base, int pr, int lane, int64_t n_pts)
+{
+    const int q = pr & 3;
+    const int64_t P = base + (pr >> 2);
+    if (p.out.field == nullptr) {
+        if (P < n_pts) {
+            if (q == 0) {
+#pragma unroll
+                for (int o = 0; o < 8; ++o)
+                    p.out.y[P * 8 + o] = v[o] + b5[o];
+            } else if (p.out.J) {
+#pragma unroll
+                for (int o = 0; o < 8; ++o)
+                    p.out.J[(P * 8 + o) * 3 + (q - 1)] = v[o];
+            }
+        }
+    } else {
+        // physical field: B = B_s y_B (AU/r)^2, E = E_s y_E (AU/r) at R = pos_scale p;
+        // gradients by the product rule with d/dR = (x_scale / pos_scale) d/dx
+        const unsigned full_mask = 0xffffffffu;
+        const int src = lane & ~3;
+        float yv[6];
+#pragma unroll
+        for (int o = 0; o < 6; ++o)
+            yv[o] = __shfl_sync(full_mask, v[o] + b5[o], src);
+        if (P < n_pts) {
+            const double au = 1.495978707e11;
+            const float ps = p.in.pos_scale;
+            const float X0 = __ldg(p.in.p + 3 * P) * ps, X1 = __ldg(p.in.p + 3 * P + 1) * ps,
+                        X2 = __ldg(p.in.p + 3 * P + 2) * ps;
+            const float r2 = X0 * X0 + X1 * X1 + X2 * X2;
+            const float ir = rsqrtf(r2);
+            const float a = (float)au * ir;                   // AU / r
+            const float bs = (float)p.out.B_scale * a * a;    // B per unit y_B
+            const float es = (float)p.out.E_scale * a;        // E per unit y_E
+            float *dst = p.out.field + P * p.out.field_stride;
+            if (q == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dst[c] = bs * yv[c];
+                    dst[3 + c] = es * yv[3 + c];
+                }
+            } else {
+                const int d = q - 1;
+                const float Xd = d == 0 ? X0 : (d == 1 ? X1 : X2);
+                const float irm = p.in.x_scale / ps;  // d/dR = (x_scale / pos_scale) d/dx
+                const float ur = Xd * ir * ir;  // R_d / r^2
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dst[6 + 3 * d + c] = bs * (v[c] * irm - 2.0f * yv[c] * ur);
+                    dst[15 + 3 * d + c] = es * (v[3 + c] * irm - yv[3 + c] * ur);
+                }
+                // the push's layout also takes grad(Phi): Phi = E_scale AU y_Phi
+                if (p.out.field_stride >= 40)
+                    dst[34 + d] = (float)(p.out.E_scale * au) * v[7] * irm;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     siren_eval_kernel(const __grid_constant__ CUtensorMap mwh, const __grid_constant__ CUtensorMap mw5,
-                      const EvalParams p)
+                      const __grid_constant__ EvalParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -122,7 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *acc = h_ready + 2;          // [2]: accumulator of a half complete
     uint64_t *kdone = acc + 2;            // half 1 has consumed input features 0-127
     uint64_t *acc_out = kdone + 1;        // output layer complete
-    uint64_t *fin = acc_out + 1;
+    uint64_t *out_a = acc_out + 1;        // output-layer MMAs over input features 0-127 complete
+    uint64_t *fin = out_a + 1;
     uint32_t *tmem_slot = (uint32_t *)(fin + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
@@ -145,6 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&acc[1], 1);
         mbar_init(kdone, 1);
         mbar_init(acc_out, 1);
+        mbar_init(out_a, 1);
         mbar_init(fin, 1);
         *abort = 0;
         mbar_fence_init();
@@ -228,22 +298,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 if (!ok) break;
-                // output layer: rows x W5^T; M-tile 0 into columns 0-15, M-tile 1 into 256-271
-                if (!wait_abort(&h_ready[0], nh0 & 1u, abort, p.err, 15)) break;
-                ++nh0;
-                if (!wait_abort(&h_ready[1], nh1 & 1u, abort, p.err, 16)) break;
-                ++nh1;
-                tc_fence_after();
+                // output layer: rows x W5^T, M-tile 0 into columns 0-15 and M-tile 1 into 16-31
+                // (both in the drained half-0 accumulator), in two K halves: input features
+                // 0-127 as soon as their epilogue is done, 128-255 after the last one
                 const uint32_t s = g % kStagesW;
-                if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 17)) break;
-                tc_fence_after();
-                const uint32_t wb = smem_u32(sW + s * kChunkBytes);
+                bool ok2 = true;
+                for (int kh = 0; kh < 2 && ok2; ++kh) {
+                    uint32_t &nh = kh ? nh1 : nh0;
+                    if (!wait_abort(&h_ready[kh], nh & 1u, abort, p.err, 15 + kh)) { ok2 = false; break; }
+                    ++nh;
+                    tc_fence_after();
+                    if (kh == 0) {
+                        if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 17)) { ok2 = false; break; }
+                        tc_fence_after();
+                    }
+                    const uint32_t wb = smem_u32(sW + s * kChunkBytes);
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
+                    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                    for (int k16 = 0; k16 < 16; ++k16)
-                        mma_bf16(tmem + mt * 256, desc_sw128_mn(hb + mt * 2048 + k16 * 8192, 1024, 4096),
-                                 desc_sw128(wb + (k16 >> 2) * 2048 + (k16 & 3) * 32), id_out, k16 ? 1u : 0u);
+                        for (int k8 = 0; k8 < 8; ++k8) {
+                            const int k16 = kh * 8 + k8;
+                            mma_bf16(tmem + mt * 16, desc_sw128_mn(hb + mt * 2048 + k16 * 8192, 1024, 4096),
+                                     desc_sw128(wb + (k16 >> 2) * 2048 + (k16 & 3) * 32), id_out, k16 ? 1u : 0u);
+                        }
+                    if (kh == 0) mma_commit(out_a);
+                }
+                if (!ok2) break;
                 mma_commit(&empty[s]);
                 ++g;
                 mma_commit(acc_out);
@@ -281,24 +361,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t *hrow1 = hrow0 + 16 * 4096;
         const uint32_t rsw = (uint32_t)(lane & 7);
         const unsigned full_mask = 0xffffffffu;
-        uint32_t na0 = 0, na1 = 0, nk = 0, no = 0;
-        bool ok = true;
+        uint32_t na0 = 0, na1 = 0, nk = 0, no = 0, noa = 0;
+        bool ok = true, first = true;
+        int64_t base_prev = 0;
+        // this warp's 16 points: lane i < 16 holds point 16 rg + i, shared by shuffles; the
+        // next tile's are fetched while the current one runs
+        float px = 0.f, py = 0.f, pz = 0.f;
+        const int pt_off = rg * 16 + (lane & 15);
+        {
+            const int64_t P = (int64_t)blockIdx.x * kPts + pt_off;
+            if (P < n_pts) {
+                px = __ldg(p.in.p + 3 * P) * p.in.x_scale;
+                py = __ldg(p.in.p + 3 * P + 1) * p.in.x_scale;
+                pz = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
+            }
+        }
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int64_t base = t * kPts;
-            // this warp's 16 points: lane i < 16 holds point 16 rg + i, shared by shuffles
-            float px = 0.f, py = 0.f, pz = 0.f;
-            {
-                const int64_t P = base + rg * 16 + (lane & 15);
-                if (P < n_pts) {
-                    px = __ldg(p.in.p + 3 * P) * p.in.x_scale;
-                    py = __ldg(p.in.p + 3 * P + 1) * p.in.x_scale;
-                    pz = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
-                }
-            }
-            // layer 1 on the CUDA cores, half 0 then half 1
+            // Layer 1 on the CUDA cores, half 0 then half 1. The previous tile's output layer
+            // still runs meanwhile: half 0 overwrites input features 0-127 once the output
+            // MMAs over them are done (out_a); before half 0 is announced, the output
+            // accumulator is read (the next MMAs overwrite it); half 1 follows the rest of the
+            // output layer (acc_out), then the previous tile's outputs are stored.
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint8_t *hrow = h ? hrow1 : hrow0;
+                if (h == 0 && !first) {
+                    if (!wait_abort(out_a, noa & 1u, abort, p.err, 21)) {
+                        ok = false;
+                        break;
+                    }
+                    ++noa;
+                }
 #pragma unroll 2
                 for (int p2 = 0; p2 < 8; ++p2) {
                     float o[8];
@@ -319,8 +413,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                     store_rows8(hrow, rsw, (uint32_t)(rg * 64 + 8 * p2), o);
                 }
                 fence_proxy_async_smem();
+                float v[16];
+                if (h == 0 && !first) {
+                    if (!wait_abort(acc_out, no & 1u, abort, p.err, 20)) {
+                        ok = false;
+                        break;
+                    }
+                    ++no;
+                    tc_fence_after();
+                    if (rg < 2) tmem_ld16(lane_base + rg * 16, v);
+                }
                 tc_fence_before();
                 mbar_arrive(&h_ready[h]);
+                if (h == 0 && !first && rg < 2)
+                    store_out(p, b5, v, base_prev, rg * 128 + lq * 32 + lane, lane, n_pts);
+            }
+            if (!ok) break;
+            {
+                const int64_t P = (t + gridDim.x) * kPts + pt_off;
+                px = py = pz = 0.f;
+                if (t + gridDim.x < n_tiles && P < n_pts) {
+                    px = __ldg(p.in.p + 3 * P) * p.in.x_scale;
+                    py = __ldg(p.in.p + 3 * P + 1) * p.in.x_scale;
+                    pz = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
+                }
             }
             // hidden layers 2-4: epilogues of D = W_k H^T, half 0 then half 1
             for (int L = 0; L < 3 && ok; ++L) {
@@ -373,70 +489,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
-            // output layer (all compute warps wait: the next tile's layer 1 overwrites H4)
-            if (!wait_abort(acc_out, no & 1u, abort, p.err, 20)) break;
-            ++no;
+            base_prev = base;
+            first = false;
+        }
+        // the last tile's output layer
+        if (ok && !first && wait_abort(acc_out, no & 1u, abort, p.err, 20)) {
             tc_fence_after();
-            if (rg >= 2) continue;
-            float v[16];
-            tmem_ld16(lane_base + rg * 256, v);
-            tc_fence_before();
-            const int pr = rg * 128 + lq * 32 + lane;
-            const int q = pr & 3;
-            const int64_t P = base + (pr >> 2);
-            if (p.out.field == nullptr) {
-                if (P < n_pts) {
-                    if (q == 0) {
-#pragma unroll
-                        for (int o = 0; o < 8; ++o)
-                            p.out.y[P * 8 + o] = v[o] + b5[o];
-                    } else if (p.out.J) {
-#pragma unroll
-                        for (int o = 0; o < 8; ++o)
-                            p.out.J[(P * 8 + o) * 3 + (q - 1)] = v[o];
-                    }
-                }
-            } else {
-                // physical field: B = B_s y_B (AU/r)^2, E = E_s y_E (AU/r) at R = pos_scale p;
-                // gradients by the product rule with d/dR = (x_scale / pos_scale) d/dx
-                const unsigned full_mask = 0xffffffffu;
-                const int src = lane & ~3;
-                float yv[6];
-#pragma unroll
-                for (int o = 0; o < 6; ++o)
-                    yv[o] = __shfl_sync(full_mask, v[o] + b5[o], src);
-                if (P < n_pts) {
-                    const double au = 1.495978707e11;
-                    const float ps = p.in.pos_scale;
-                    const float X0 = __ldg(p.in.p + 3 * P) * ps, X1 = __ldg(p.in.p + 3 * P + 1) * ps,
-                                X2 = __ldg(p.in.p + 3 * P + 2) * ps;
-                    const float r2 = X0 * X0 + X1 * X1 + X2 * X2;
-                    const float ir = rsqrtf(r2);
-                    const float a = (float)au * ir;                   // AU / r
-                    const float bs = (float)p.out.B_scale * a * a;    // B per unit y_B
-                    const float es = (float)p.out.E_scale * a;        // E per unit y_E
-                    float *dst = p.out.field + P * p.out.field_stride;
-                    if (q == 0) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            dst[c] = bs * yv[c];
-                            dst[3 + c] = es * yv[3 + c];
-                        }
-                    } else {
-                        const int d = q - 1;
-                        const float Xd = d == 0 ? X0 : (d == 1 ? X1 : X2);
-                        const float irm = p.in.x_scale / ps;  // d/dR = (x_scale / pos_scale) d/dx
-                        const float ur = Xd * ir * ir;  // R_d / r^2
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            dst[6 + 3 * d + c] = bs * (v[c] * irm - 2.0f * yv[c] * ur);
-                            dst[15 + 3 * d + c] = es * (v[3 + c] * irm - yv[3 + c] * ur);
-                        }
-                        // the push's layout also takes grad(Phi): Phi = E_scale AU y_Phi
-                        if (p.out.field_stride >= 40)
-                            dst[34 + d] = (float)(p.out.E_scale * au) * v[7] * irm;
-                    }
-                }
+            if (rg < 2) {
+                float v[16];
+                tmem_ld16(lane_base + rg * 16, v);
+                store_out(p, b5, v, base_prev, rg * 128 + lq * 32 + lane, lane, n_pts);
             }
         }
     }
