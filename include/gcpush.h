@@ -38,7 +38,7 @@ enum {
     GC_ERR_NOMEM = -3,          /* device or pinned host allocation failed */
     GC_ERR_STATE = -4,          /* call out of order (e.g. advance before field_load) */
     GC_ERR_DEVICE_ANOMALY = -5, /* particles were flagged during the call (see gc_stats) */
-    GC_ERR_UNSUPPORTED = -6     /* feature not available in this build or precision */
+    GC_ERR_UNSUPPORTED = -6     /* feature not available for this field source or precision */
 };
 
 /* precision of the push */
