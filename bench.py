@@ -45,6 +45,7 @@ UNIT = "particle-steps/s"
 FLOP_PER_PSTEP = 2 * (236 + 319) + 121
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300
 # DRAM bytes (read + write) of one push launch of the default workload (3x10^6 particles,
 # 1000 steps per launch), from one ncu capture of the current kernel
 # (profiles/push_kernel_fp32_parker256_3e6.md); reported only for that launch shape
@@ -513,8 +514,13 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        fp64 = {"value": world * n_rank * n64 / (ms / 1e3), "unit": UNIT, "push_steps": n64,
-                "note": "same workload, FP64 grid and arithmetic; timed after the same start-up"}
+        v64 = world * n_rank * n64 / (ms / 1e3)
+        a64 = FLOP_PER_PSTEP * v64 / world / 1e12
+        fp64 = {"value": v64, "unit": UNIT, "push_steps": n64,
+                "note": "same workload, FP64 grid and arithmetic; timed after the same start-up",
+                "roofline": {"bound": "fp64", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a64 / FP64_PEAK_TFLOPS, "flop_per_particle_step": FLOP_PER_PSTEP,
+                             "peak_basis": "nominal GB300 FP64 rate (no measured figure)"}}
         c64.close()
 
     # ---------------- 64 uneven ensembles, graph replay, autotuned launch shape -------------
