@@ -202,55 +202,13 @@ __device__ __forceinline__ void p2_split(unsigned long long v, float &lo, float 
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// Trilinear interpolation in (r, theta, phi) index space with the index-space gradient of
-// the interpolant (Sect. 2.2). Node-centred grid, poles included in theta, periodic in phi.
-// Positions more than one radial cell outside the grid are flagged; beyond the edge nodes
-// the interpolant is extended as a constant.
-template <typename T, int POT = POT_RUNTIME>
-__device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sample<T> &s)
+// The trilinear interpolant of one node array at a located point (cell offsets o0 / o1 of
+// the two phi planes, theta-row stride nr8, fractions fr, ft, fp): values and index-space
+// derivatives of B and E, and of the potential channel when use_pot.
+template <typename T>
+__device__ __forceinline__ void interp_nodes(const T *__restrict__ nodes, uint32_t o0, uint32_t o1, uint32_t nr8,
+                                             T fr, T ft, T fp, bool use_pot, Sample<T> &s)
 {
-    uint32_t flags = 0;
-    T rho2 = x * x + y * y;
-    if (!(rho2 > T(1e-30))) {
-        flags |= FLAG_AXIS;
-        rho2 = T(1e-30);
-    }
-    const T r2 = rho2 + z * z;
-    const T inv_rho = m_rsqrt(rho2), inv_r = m_rsqrt(r2);
-    const T rho = rho2 * inv_rho, r = r2 * inv_r;
-    const T theta = m_atan2(rho, z);
-    T phi = m_atan2(y, x);
-    if (phi < T(0))
-        phi += two_pi<T>();
-    T xr = (r - gm.r_min) * gm.inv_dr;
-    T xt = theta * gm.inv_dth;
-    T xp = phi * gm.inv_dph;
-    if (!(m_finite(xr) && m_finite(xt) && m_finite(xp))) {
-        flags |= FLAG_NONFINITE;
-        xr = T(0); xt = T(0); xp = T(0);
-    }
-    if (xr < T(-1) || xr > T(gm.n_r))
-        flags |= FLAG_OUT_OF_GRID;
-
-    int i = (int)m_floor(xr);
-    T fr = xr - T(i);
-    if (i < 0) { i = 0; fr = T(0); }
-    else if (i > gm.n_r - 2) { i = gm.n_r - 2; fr = T(1); }
-    int j = (int)m_floor(xt);
-    T ft = xt - T(j);
-    if (j < 0) { j = 0; ft = T(0); }
-    else if (j > gm.n_th - 2) { j = gm.n_th - 2; ft = T(1); }
-    int k = (int)m_floor(xp);
-    const T fp = xp - T(k);
-    if (k >= gm.n_ph) k -= gm.n_ph;
-    if (k < 0) k += gm.n_ph;
-    const int k1 = (k + 1 == gm.n_ph) ? 0 : k + 1;
-
-    const uint32_t nr8 = (uint32_t)gm.n_r * 8u;
-    const uint32_t o0 = (((uint32_t)k * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
-    const uint32_t o1 = (((uint32_t)k1 * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
-
-    const bool use_pot = POT == POT_ON || (POT == POT_RUNTIME && gm.ideal == 2);
     // FP32: each 32-byte node record in one 256-bit load, as four packed channel pairs
     // (Bx By | Bz Ex | Ey Ez | |B| Phi), interpolated two channels at a time (the fourth
     // pair for the potential's gradient only)
@@ -260,7 +218,7 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
         for (int b = 0; b < 2; ++b) {
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                const float *p = (const float *)gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
+                const float *p = (const float *)nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
                     load_node_pairs(p + 8 * a, c2[b][cc][a]);
@@ -317,7 +275,7 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     for (int b = 0; b < 2; ++b) {
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-            const T *p = gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
+            const T *p = nodes + (cc ? o1 : o0) + (b ? nr8 : 0u);
             load_node(p, c[b][cc][0]);
             load_node(p + 8, c[b][cc][1]);
         }
@@ -367,7 +325,7 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
             for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
-                    ph[b][cc][a] = __ldg(gm.nodes + (cc ? o1 : o0) + (b ? nr8 : 0u) + 8 * a + 7);
+                    ph[b][cc][a] = __ldg(nodes + (cc ? o1 : o0) + (b ? nr8 : 0u) + 8 * a + 7);
         T L[2][2], D[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b)
@@ -390,6 +348,62 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
         s.dPhi[0] = s.dPhi[1] = s.dPhi[2] = T(0);
     }
 
+}
+
+// Trilinear interpolation in (r, theta, phi) index space with the index-space gradient of
+// the interpolant (Sect. 2.2). Node-centred grid, poles included in theta, periodic in phi.
+// Positions more than one radial cell outside the grid are flagged; beyond the edge nodes
+// the interpolant is extended as a constant.
+template <typename T, int POT = POT_RUNTIME>
+__device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sample<T> &s,
+                                       Sample<T> *s1 = nullptr)
+{
+    uint32_t flags = 0;
+    T rho2 = x * x + y * y;
+    if (!(rho2 > T(1e-30))) {
+        flags |= FLAG_AXIS;
+        rho2 = T(1e-30);
+    }
+    const T r2 = rho2 + z * z;
+    const T inv_rho = m_rsqrt(rho2), inv_r = m_rsqrt(r2);
+    const T rho = rho2 * inv_rho, r = r2 * inv_r;
+    const T theta = m_atan2(rho, z);
+    T phi = m_atan2(y, x);
+    if (phi < T(0))
+        phi += two_pi<T>();
+    T xr = (r - gm.r_min) * gm.inv_dr;
+    T xt = theta * gm.inv_dth;
+    T xp = phi * gm.inv_dph;
+    if (!(m_finite(xr) && m_finite(xt) && m_finite(xp))) {
+        flags |= FLAG_NONFINITE;
+        xr = T(0); xt = T(0); xp = T(0);
+    }
+    if (xr < T(-1) || xr > T(gm.n_r))
+        flags |= FLAG_OUT_OF_GRID;
+
+    int i = (int)m_floor(xr);
+    T fr = xr - T(i);
+    if (i < 0) { i = 0; fr = T(0); }
+    else if (i > gm.n_r - 2) { i = gm.n_r - 2; fr = T(1); }
+    int j = (int)m_floor(xt);
+    T ft = xt - T(j);
+    if (j < 0) { j = 0; ft = T(0); }
+    else if (j > gm.n_th - 2) { j = gm.n_th - 2; ft = T(1); }
+    int k = (int)m_floor(xp);
+    const T fp = xp - T(k);
+    if (k >= gm.n_ph) k -= gm.n_ph;
+    if (k < 0) k += gm.n_ph;
+    const int k1 = (k + 1 == gm.n_ph) ? 0 : k + 1;
+
+    const uint32_t nr8 = (uint32_t)gm.n_r * 8u;
+    const uint32_t o0 = (((uint32_t)k * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
+    const uint32_t o1 = (((uint32_t)k1 * (uint32_t)gm.n_th + (uint32_t)j) * (uint32_t)gm.n_r + (uint32_t)i) * 8u;
+
+    const bool use_pot = POT == POT_ON || (POT == POT_RUNTIME && gm.ideal == 2);
+    interp_nodes<T>(gm.nodes, o0, o1, nr8, fr, ft, fp, use_pot, s);
+    if (s1)  // time-dependent fields: the second snapshot at the same point
+        interp_nodes<T>(gm.nodes1, o0, o1, nr8, fr, ft, fp, use_pot, *s1);
+
     // Cartesian gradients of the index coordinates: rhat/dr, thetahat/(r dtheta),
     // phihat/(r sin(theta) dphi)
     const T sr = inv_r * gm.inv_dr;
@@ -402,17 +416,15 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     s.flags = flags;
 }
 
-// Time-dependent fields: both snapshots gathered at the point, every quantity blended
-// linearly at t_rel seconds after the first snapshot (held constant outside the window),
-// and the time derivatives taken as the snapshots' secant slope inside it.
+// Time-dependent fields: both snapshots interpolated at the point (located once), every
+// quantity blended linearly at t_rel seconds after the first snapshot (held constant
+// outside the window), and the time derivatives taken as the snapshots' secant slope
+// inside it.
 template <typename T, int POT = POT_RUNTIME>
 __device__ __forceinline__ void gather_td(const GridMeta<T> &gm, T x, T y, T z, T t_rel, Sample<T> &s)
 {
-    gather<T, POT>(gm, x, y, z, s);
-    GridMeta<T> g1 = gm;
-    g1.nodes = gm.nodes1;
     Sample<T> s1;
-    gather<T, POT>(g1, x, y, z, s1);
+    gather<T, POT>(gm, x, y, z, s, &s1);
     // the window test on the time itself: at t_rel == span the weight may round above 1
     const bool inside = (t_rel >= T(0)) && (t_rel <= gm.span);
     T w = t_rel * gm.inv_span;
@@ -431,7 +443,6 @@ __device__ __forceinline__ void gather_td(const GridMeta<T> &gm, T x, T y, T z, 
             s.dE[d][c] += w * (s1.dE[d][c] - s.dE[d][c]);
         }
     }
-    s.flags |= s1.flags;
 }
 
 // ----------------------------------------------------------------------------------------
