@@ -17,7 +17,11 @@
  *     particle state and grid values are SI (m, m/s, J/T, T, V/m).
  *   - Work is issued on the context's CUDA stream (gc_options.stream). Calls
  *     that return data to the host synchronise that stream before returning.
- *   - A context is not thread-safe; use one context per host thread.
+ *   - A context is not thread-safe; use one context per host thread. Contexts on the
+ *     same device, each on its own stream and driven by its own thread, run
+ *     concurrently (one context's host copies overlap another's kernels); a
+ *     population split into such shards evolves exactly as in one context when
+ *     each shard keeps its particle ids (gc_options.id_base).
  */
 #ifndef GCPUSH_H
 #define GCPUSH_H
@@ -204,7 +208,14 @@ int gc_advance(gc_ctx *ctx, double dt, int64_t n_steps, double lambda_au);
 int gc_tally(gc_ctx *ctx, const gc_tally_desc *arm, gc_tally_out *out);
 
 /* Copy the particle state to / from host arrays (in id order of the last set/inject;
- * the library may reorder particles internally, get returns them in that order). */
+ * the library may reorder particles internally, get returns them in that order).
+ * Every array of the gc_particle_soa holds out_host->n / in_host->n entries (F0 and F1
+ * as [4][n]); pinned host memory makes the copies fastest. get: n must equal the
+ * context's particle count (GC_ERR_INVALID otherwise); a NULL array is skipped. set:
+ * replaces the whole state (every array required; ensemble ids must name injected
+ * ensembles, else GC_ERR_INVALID and the old state is kept); the next gc_advance treats
+ * the state as unsorted. Both synchronise the context's stream before returning. Used for
+ * checkpoints (with gc_set_clock) and for host-side analysis. */
 int gc_particles_get(gc_ctx *ctx, gc_particle_soa *out_host);
 int gc_particles_set(gc_ctx *ctx, const gc_particle_soa *in_host);
 

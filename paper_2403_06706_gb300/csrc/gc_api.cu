@@ -1407,6 +1407,9 @@ int gc_particles_set(gc_ctx *c, const gc_particle_soa *in)
     }
     c->n = n;
     c->st.n = n;
+    // a state from the host is in id order, not in cell order: sort before the next push
+    if (c->sort_every > 0)
+        c->steps_since_sort = c->sort_every;
     c->in_id_order = ascending;
     c->ids_dense = dense;
     c->id_lo = n ? lo : c->next_id;
