@@ -93,9 +93,6 @@ __device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, 
 __device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ bool m_finite(float a) { return isfinite(a); }
 __device__ __forceinline__ bool m_finite(double a) { return isfinite(a); }
-template <typename T> __device__ __forceinline__ T m_inf();
-template <> __device__ __forceinline__ float m_inf<float>() { return __int_as_float(0x7f800000); }
-template <> __device__ __forceinline__ double m_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
 template <typename T> __device__ __forceinline__ T two_pi();
 template <> __device__ __forceinline__ float two_pi<float>() { return 6.28318530717958647692f; }
 template <> __device__ __forceinline__ double two_pi<double>() { return 6.28318530717958647692; }
@@ -377,8 +374,7 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     T xr = (r - gm.r_min) * gm.inv_dr;
     T xt = theta * gm.inv_dth;
     T xp = phi * gm.inv_dph;
-    // one test for all three: a NaN or an infinity makes the sum non-finite
-    if (!(fabs(xr) + fabs(xt) + fabs(xp) < m_inf<T>())) {
+    if (!(m_finite(xr) && m_finite(xt) && m_finite(xp))) {
         flags |= FLAG_NONFINITE;
         xr = T(0); xt = T(0); xp = T(0);
     }
