@@ -70,9 +70,11 @@ ENS = (synth.EnsembleSpec(700, lam_au=0.05, r_out_au=2.4),
 TALLY = dict(cadence=50, n_mu=8, n_E=8, n_r=16, n_age=8, age_max_s=500.0)
 
 
-def _run(graph, nodes, calls=4, n=120):
+def _run(graph, nodes, calls=4, n=120, nodes1=None):
     with gcpush.Context(precision=gcpush.PREC_FP32_MIXED, seed=21) as c:
         c.field_load(nodes, WIND.r_min_au, WIND.r_max_au)
+        if nodes1 is not None:
+            c.field_load_next(nodes1, 0.0, 300.0)
         c.inject(list(ENS))
         c.set_launch(block=64, steps_per_launch=60, sort_every=90, grid_waves=2)
         c.tally_arm(**TALLY)
@@ -82,10 +84,20 @@ def _run(graph, nodes, calls=4, n=120):
         return c.get_state(), c.tally_read(), c.stats()
 
 
-def test_graph_replay_is_bitwise_equal_to_direct_path():
+@pytest.mark.parametrize("time_dependent", [False, True])
+def test_graph_replay_is_bitwise_equal_to_direct_path(time_dependent):
+    """Graph replay against direct launches; with a time-dependent field the replayed
+    kernels take the call's time from device memory, so the blend must still follow it."""
     nodes = synth.wind_grid(WIND, dtype=np.float32)
-    a, ta, sa = _run(False, nodes)
-    b, tb, sb = _run(True, nodes)
+    nodes1 = None
+    if time_dependent:
+        nodes1 = synth.wind_grid(synth.WindSpec(64, 32, 64, B1=4.2e-9, u_sw=5.0e5, eps=0.15, n_modes=4,
+                                                seed=3), dtype=np.float32)
+    a, ta, sa = _run(False, nodes, nodes1=nodes1)
+    b, tb, sb = _run(True, nodes, nodes1=nodes1)
+    if time_dependent:
+        c, _, _ = _run(False, nodes)
+        assert np.abs(a["u"] - c["u"]).max() > 0
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
     for k in ta:
