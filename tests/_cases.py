@@ -109,7 +109,10 @@ def compare_states(g, o, tol, pm, skip=None, lam=None):
     mscale = np.maximum(np.abs(o["mub"][keep]), 1e-30 + np.abs(o["mub_inj"][keep]).max() * 1e-6)
     out["mub"] = np.max(np.abs(g["mub"][keep] - o["mub"][keep]) / mscale)
     for F in ("F0", "F1"):
-        v = np.linalg.norm(o[F][:3, keep], axis=0)
+        # dR/dt = v_par b + drifts: near a mirror point v_par -> 0 and |dR/dt| shrinks to the
+        # drift speed while its error still follows the v_par error, which scales with |p|/m;
+        # so the scale is |dR/dt| but not below a tenth of |p|/m
+        v = np.maximum(np.linalg.norm(o[F][:3, keep], axis=0), 0.1 * pm[keep])
         out[F + "_R"] = np.max(np.linalg.norm(g[F][:3, keep] - o[F][:3, keep], axis=0) / v)
         # d(gamma v_par)/dt: the mirror force is ~ v^2 / L ~ (|p|/m) / 1000 s
         out[F + "_u"] = np.max(np.abs(g[F][3, keep] - o[F][3, keep]) / (pm[keep] / 1000.0))
