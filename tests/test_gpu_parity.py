@@ -382,3 +382,24 @@ def test_time_dependent_field_host_rules(nodes32):
     b, _, _ = run_gpu(nodes32, WIND, ENS, calls, gcpush.PREC_FP32_MIXED, seed=3)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_degenerate_mean_free_paths(nodes64):
+    """The two limits of the scattering: lambda = 1e-4 AU (a collision in nearly every step,
+    at most one per step, with the start-up history rebuilt after each) and lambda = 100 AU
+    (no collision in the run), FP64 against the oracle at 1e-9."""
+    ens = (synth.EnsembleSpec(64, lam_au=1e-4, r_out_au=R_OUT),
+           synth.EnsembleSpec(64, r0_au=0.6, lat_deg=-12.0, lon_deg=33.0, lam_au=100.0, r_out_au=R_OUT))
+    calls = [(0.5, 200, 0.0)]
+    g, _, gs = run_gpu(nodes64, WIND, ens, calls, gcpush.PREC_FP64, seed=31)
+    o, _, os_ = run_oracle(nodes64, WIND, ens, calls, seed=31)
+    _ints_equal(g, o)
+    err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes64, WIND, ens),
+                         lam=np.array([e.lam_au for e in ens])[o["ens"].astype(int)] * AU)
+    for k, v in err.items():
+        assert v < 1e-9, (k, v, err)
+    # the short-path particles collide in most steps (rebirths at the inner shell reset their
+    # counts), the long-path ones never
+    short, long_ = g["ens"] == 0, g["ens"] == 1
+    assert g["ncoll"][short].max() <= 200 and g["ncoll"][long_].max() == 0
+    assert gs["collisions"] == os_[0] > 0.4 * 64 * 200
