@@ -499,14 +499,6 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
     for (int c = 0; c < 3; ++c)
         b[c] = s.B[c] * inv_B;
 
-    // index-space projections of b
-    T pb[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        pb[d] = dot3(s.g[d], b);
-    T JBb[3], JEb[3];
-    jvec(s.dB, pb, JBb);
-    jvec(s.dE, pb, JEb);
     // grad|B| = J_B^T b
     T sb[3];
 #pragma unroll
@@ -517,51 +509,26 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
     for (int jx = 0; jx < 3; ++jx)
         gB[jx] = sb[0] * s.g[0][jx] + sb[1] * s.g[1][jx] + sb[2] * s.g[2][jx];
     const T b_gB = dot3(b, gB);
-    // curvature (b.grad)b = (J_B b - b (b.grad|B|)) / |B|
-    T kap[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        kap[c] = (JBb[c] - b[c] * b_gB) * inv_B;
 
-    // E x B drift and its directional derivatives
+    // E x B drift
     T vE[3];
     cross3(s.E, s.B, vE);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         vE[c] *= inv_B2;
-    T pv[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        pv[d] = dot3(s.g[d], vE);
-    T JBv[3], JEv[3];
-    jvec(s.dB, pv, JBv);
-    jvec(s.dE, pv, JEv);
-    const T v_gB = dot3(vE, gB);
-    // (v_E.grad) b
-    T vgb[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        vgb[c] = (JBv[c] - b[c] * v_gB) * inv_B;
-    // (w.grad) v_E = ((J_E w) x B + E x (J_B w)) / B^2 - 2 v_E (w.grad|B|) / |B|
-    T t1[3], t2[3], bgv[3], vgv[3];
-    cross3(JEb, s.B, t1);
-    cross3(s.E, JBb, t2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        bgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * b_gB * inv_B;
-    cross3(JEv, s.B, t1);
-    cross3(s.E, JBv, t2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        vgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * v_gB * inv_B;
 
     // ideal 1: E_par = 0 (ideal Ohm's law); 0: the interpolated E.b; 2: the two-fluid
     // correction -grad(Phi) (Sect. 2.2): E_par = -b.grad(Phi) = -sum_d dPhi/di_d (g_d . b)
     T Epar;
-    if (POT == POT_ON || (POT == POT_RUNTIME && ideal == 2))
+    if (POT == POT_ON || (POT == POT_RUNTIME && ideal == 2)) {
+        T pb[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            pb[d] = dot3(s.g[d], b);
         Epar = -(s.dPhi[0] * pb[0] + s.dPhi[1] * pb[1] + s.dPhi[2] * pb[2]);
-    else
+    } else {
         Epar = ideal ? T(0) : dot3(s.E, b);
+    }
     // gamma^2 = 1 + (gamma v)^2 / c^2 with (gamma v)^2 = u^2 + 2 mu_B B / m
     const T g2 = T(1) + (u * u + T(2) * mub * Bm * ph.inv_m) * ph.inv_c2;
     const T inv_g = m_rsqrt(g2);
@@ -574,14 +541,42 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
             F[c] = vpar * b[c];
         F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB;
     } else {
+        // Every directional derivative of Eqs. 1-2 is along w = v_par b + v_E (the guiding
+        // centre's velocity without the drifts): the bracket's v_par^2 (b.grad)b +
+        // v_par (v_E.grad)b = v_par (w.grad)b and v_par (b.grad)v_E + (v_E.grad)v_E =
+        // (w.grad)v_E, and Eq. 2's v_par (b.grad)b + (v_E.grad)b = (w.grad)b.
+        T wv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            wv[c] = vpar * b[c] + vE[c];
+        T pw[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            pw[d] = dot3(s.g[d], wv);
+        T JBw[3], JEw[3];
+        jvec(s.dB, pw, JBw);
+        jvec(s.dE, pw, JEw);
+        const T w_gB = dot3(wv, gB);
+        // (w.grad)b = (J_B w - b (w.grad|B|)) / |B|
+        T wgb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            wgb[c] = (JBw[c] - b[c] * w_gB) * inv_B;
+        // (w.grad)v_E = ((J_E w) x B + E x (J_B w)) / B^2 - 2 v_E (w.grad|B|) / |B|
+        T t1[3], t2[3], wgv[3];
+        cross3(JEw, s.B, t1);
+        cross3(s.E, JBw, t2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            wgv[c] = (t1[c] + t2[c]) * inv_B2 - T(2) * vE[c] * w_gB * inv_B;
+
         // Eq. 1 bracket
         const T c_gB = mub * ph.inv_m * inv_g * inv_g;
         const T c_vE = ph.qm * vpar * Epar * ph.inv_c2 * inv_g;
-        const T v2 = vpar * vpar;
         T br[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            br[c] = c_gB * gB[c] + c_vE * vE[c] + v2 * kap[c] + vpar * (vgb[c] + bgv[c]) + vgv[c];
+            br[c] = c_gB * gB[c] + c_vE * vE[c] + vpar * wgb[c] + wgv[c];
         // time-dependent fields: v_par db/dt + dv_E/dt in the bracket, and db/dt in Eq. 2's
         // v_E product, with db/dt = (dB/dt - b (b.dB/dt)) / B and
         // dv_E/dt = (dE/dt x B + E x dB/dt) / B^2 - 2 v_E (b.dB/dt) / B
@@ -604,11 +599,11 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         for (int c = 0; c < 3; ++c)
             F[c] = vpar * b[c] + vE[c] + pre * bxbr[c];
         // Eq. 2
-        T w[3];
+        T w2[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            w[c] = vpar * kap[c] + vgb[c] + dbdt[c];
-        F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB + gamma * dot3(vE, w);
+            w2[c] = wgb[c] + dbdt[c];
+        F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB + gamma * dot3(vE, w2);
     }
     aux.gamma = gamma;
     aux.vpar = vpar;
