@@ -197,6 +197,20 @@ __device__ __forceinline__ unsigned long long p2_bcast(float x)
     return d;
 }
 
+__device__ __forceinline__ unsigned long long p2_pack(float lo, float hi)
+{
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long p2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ void p2_split(unsigned long long v, float &lo, float &hi)
 {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
@@ -486,6 +500,38 @@ __device__ __forceinline__ void jvec(const T dF[3][3], const T p[3], T out[3])
         out[c] = dF[0][c] * p[0] + dF[1][c] * p[1] + dF[2][c] * p[2];
 }
 
+// J_B p and J_E p together; FP32: the six channels as three packed pairs (Bx By | Bz Ex |
+// Ey Ez), the pairs the gather interpolated, two FMAs per instruction
+template <typename T>
+__device__ __forceinline__ void jvec2(const T dB[3][3], const T dE[3][3], const T p[3], T JB[3], T JE[3])
+{
+    if constexpr (sizeof(T) == 4) {
+        unsigned long long acc[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const unsigned long long P = p2_bcast(p[d]);
+            const unsigned long long q0 = p2_pack(dB[d][0], dB[d][1]);
+            const unsigned long long q1 = p2_pack(dB[d][2], dE[d][0]);
+            const unsigned long long q2 = p2_pack(dE[d][1], dE[d][2]);
+            if (d == 0) {
+                acc[0] = p2_mul(q0, P);
+                acc[1] = p2_mul(q1, P);
+                acc[2] = p2_mul(q2, P);
+            } else {
+                acc[0] = p2_fma(q0, P, acc[0]);
+                acc[1] = p2_fma(q1, P, acc[1]);
+                acc[2] = p2_fma(q2, P, acc[2]);
+            }
+        }
+        p2_split(acc[0], JB[0], JB[1]);
+        p2_split(acc[1], JB[2], JE[0]);
+        p2_split(acc[2], JE[1], JE[2]);
+    } else {
+        jvec(dB, p, JB);
+        jvec(dE, p, JE);
+    }
+}
+
 template <typename T, bool TD = false, int POT = POT_RUNTIME>
 __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int ideal, T u, T mub,
                                     T F[4], Aux<T> &aux)
@@ -554,8 +600,7 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         for (int d = 0; d < 3; ++d)
             pw[d] = dot3(s.g[d], wv);
         T JBw[3], JEw[3];
-        jvec(s.dB, pw, JBw);
-        jvec(s.dE, pw, JEw);
+        jvec2(s.dB, s.dE, pw, JBw, JEw);
         const T w_gB = dot3(wv, gB);
         // (w.grad)b = (J_B w - b (w.grad|B|)) / |B|
         T wgb[3];
