@@ -54,7 +54,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300
 # DRAM bytes (read + write) of one push launch of the default workload (3x10^6 particles,
 # 1000 steps per launch), from one ncu capture of the current kernel
 # (profiles/push_kernel_fp32_parker256_3e6.md); reported only for that launch shape
-PUSH_TRAFFIC_BYTES = 492_387_000 + 373_549_000
+PUSH_TRAFFIC_BYTES = 491_188_000 + 373_183_000
 PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 # Neural field: tensor-core work of one evaluation with its Jacobian (value + 3 tangent
