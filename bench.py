@@ -237,7 +237,9 @@ def neural_bench(args, nodes, local, stream, rank):
     xs = torch.from_numpy(synth.siren_samples(X["n_samples"], w)).to("cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss = c.field_fit(xs, n_epochs=epochs, batch=X["batch"], lr=X["lr"])
+    schedule = X["schedule"] if args.neural_epochs is None else ((epochs, X["lr"]),)
+    losses = [c.field_fit(xs, n_epochs=ep, batch=X["batch"], lr=lr) for ep, lr in schedule]
+    loss = np.concatenate(losses)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     del xs
@@ -283,8 +285,9 @@ def neural_bench(args, nodes, local, stream, rank):
                      "peak_basis": "measured bf16 cuBLAS, sustained (MEASURED_PEAKS.json)",
                      "flop_per_eval": NEURAL_FLOP_PER_EVAL, "evals": evals,
                      "eval_share_of_step": fms / ms},
-        "training": {"samples": X["n_samples"], "epochs": epochs, "batch": X["batch"], "lr": X["lr"],
-                     "seconds": t_fit, "samples_per_s": X["n_samples"] * epochs / t_fit,
+        "training": {"samples": X["n_samples"], "epochs": sum(ep for ep, _ in schedule), "batch": X["batch"],
+                     "schedule": [[ep, lr] for ep, lr in schedule],
+                     "seconds": t_fit, "samples_per_s": X["n_samples"] * sum(ep for ep, _ in schedule) / t_fit,
                      "loss_first_epoch": float(loss[0]) if len(loss) else None,
                      "loss_last_epoch": float(loss[-1]) if len(loss) else None},
         "field_rel_rms_vs_grid": err,

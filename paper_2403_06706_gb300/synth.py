@@ -282,5 +282,7 @@ def c4_neural(n: int = 10_000_000) -> Workload:
     w = WindSpec(256, 128, 256, eps=0.1, n_modes=8)
     e = EnsembleSpec(n, lam_au=0.5, r_out_au=r_out_default(w))
     return Workload("siren_parker256x128x256_eps0.1_8modes_1e7e", w, (e,), 0.5, 172800, "f32",
-                    extra={"n_samples": 10_000_000, "epochs": 10, "batch": 65536, "lr": 2e-4,
+                    extra={"n_samples": 10_000_000, "epochs": 50, "batch": 65536, "lr": 4e-4,
+                           # Adam's step halved after 20, 30 and 40 epochs
+                           "schedule": ((20, 4e-4), (10, 2e-4), (10, 1e-4), (10, 5e-5)),
                            "omega0": SIREN_OMEGA0})

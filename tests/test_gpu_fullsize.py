@@ -133,7 +133,9 @@ def test_neural_workload_sampled_parity():
         c.field_load(nodes, w.r_min_au, w.r_max_au)
         c.siren_set(synth.siren_init(seed=0), omega0=X["omega0"], r_max_au=w.r_max_au, B_scale=w.B1,
                     E_scale=w.B1 * w.u_sw)
-        c.field_fit(synth.siren_samples(X["n_samples"], w), n_epochs=X["epochs"], batch=X["batch"], lr=X["lr"])
+        samples = synth.siren_samples(X["n_samples"], w)
+        for ep, lr in X["schedule"]:  # the benchmark's training schedule
+            c.field_fit(samples, n_epochs=ep, batch=X["batch"], lr=lr)
         P = c.siren_get()
         c.field_select(gcpush.FIELD_SIREN)
         c.inject(list(wn.ensembles))
