@@ -55,6 +55,10 @@ FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300
 # 1000 steps per launch), from one ncu capture of the current kernel
 # (profiles/push_kernel_fp32_parker256_3e6.md); reported only for that launch shape
 PUSH_TRAFFIC_BYTES = 491_188_000 + 373_183_000
+# thread instructions one particle-step of the FP32 push issues (smsp__inst_executed x
+# threads per warp instruction / particle-steps, same capture): the kernel is issue-bound,
+# and 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / this count is its issue ceiling
+PUSH_THREAD_INSTR_PER_PSTEP = 1005
 PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 # Neural field: tensor-core work of one evaluation with its Jacobian (value + 3 tangent
@@ -473,6 +477,10 @@ def main():
                 "kernel": "push_kernel<float>", "launch_ms": push_ms,
                 "flop_per_particle_step": FLOP_PER_PSTEP,
                 "frac_at_nominal_2kflop": (FLOP_PER_PSTEP_NOMINAL / FLOP_PER_PSTEP) * achieved / FP32_PEAK_TFLOPS,
+                "issue": {"thread_instr_per_particle_step": PUSH_THREAD_INSTR_PER_PSTEP,
+                          "ceiling_particle_steps_per_s": 152 * 4 * 32 * 2.07e9 / PUSH_THREAD_INSTR_PER_PSTEP,
+                          "frac": (n_rank * steps_per_launch / (push_ms / 1e3))
+                          / (152 * 4 * 32 * 2.07e9 / PUSH_THREAD_INSTR_PER_PSTEP)},
                 "peak_basis": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)",
                 "push_share_of_step": (s1["push_ms"] - s0["push_ms"]) / el_ms}
     gpu_launches = s1["kernel_launches"] - s0["kernel_launches"]
