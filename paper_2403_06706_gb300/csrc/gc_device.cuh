@@ -13,6 +13,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "unit_circle_table.h"
+
 namespace gcp {
 
 enum : uint32_t { FLAG_OUT_OF_GRID = 1u, FLAG_AXIS = 2u, FLAG_NONFINITE = 4u };
@@ -79,12 +81,14 @@ __device__ __forceinline__ df df_add(df a, float b)
 }
 
 // ----------------------------------------------------------------------------------------
-// precision helpers. FP64: correctly rounded library functions (the plain path). FP32:
-// fast forms whose few-ulp errors sit far below the FP32 path's 1e-4 tolerance.
+// precision helpers. FP64: library functions of at most a few ulp (the plain path; rsqrt is
+// the library's 1-ulp reciprocal square root, a fraction of the double-pipe work of a
+// correctly rounded square root followed by a division). FP32: fast forms whose few-ulp
+// errors sit far below the FP32 path's 1e-4 tolerance.
 __device__ __forceinline__ float m_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double m_sqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float m_rsqrt(float a) { return rsqrtf(a); }
-__device__ __forceinline__ double m_rsqrt(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ double m_rsqrt(double a) { return rsqrt(a); }
 __device__ __forceinline__ float m_floor(float a) { return floorf(a); }
 __device__ __forceinline__ double m_floor(double a) { return floor(a); }
 __device__ __forceinline__ float m_rcp(float a) { return __fdividef(1.0f, a); }
@@ -96,8 +100,6 @@ __device__ __forceinline__ bool m_finite(double a) { return isfinite(a); }
 template <typename T> __device__ __forceinline__ T two_pi();
 template <> __device__ __forceinline__ float two_pi<float>() { return 6.28318530717958647692f; }
 template <> __device__ __forceinline__ double two_pi<double>() { return 6.28318530717958647692; }
-
-__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
 
 // FP32 atan2: reduce to t = min(|x|,|y|) / max(|x|,|y|) in [0, 1], atan(t) ~ t p(t^2) with
 // p of degree 7 fitted for minimal maximum error on [0, 1] (|error| < 4e-8; the fit is
@@ -120,6 +122,41 @@ __device__ __forceinline__ float m_atan2(float y, float x)
     if (ay > ax) r = 1.57079632679489662f - r;
     if (x < 0.0f) r = 3.14159265358979324f - r;
     return copysignf(r, y);
+}
+
+// FP64 polar angle of (X, Y) given inv_h = 1 / hypot(X, Y) and an FP32 estimate `est` of
+// the angle (within 1e-6 rad), without a double-precision atan2. Take the reference angle
+// a_m = m (2 pi / 256) nearest the estimate, with its cosine c and sine s from a table; the
+// offset d = angle - a_m satisfies sin d = (Y c - X s) / hypot(X, Y) and |d| < 0.0123, so the
+// arcsine's Maclaurin series d = t + t^3/6 + 3 t^5/40 + 5 t^7/112 (t = sin d) leaves a
+// truncation error below 2e-19 and the result is as accurate as a library atan2 (the
+// rounding of Y c - X s, about 2e-16 rad). Returns a_m + d: in (-0.0123, 2 pi) for any
+// estimate in [-pi, pi].
+__device__ __forceinline__ double refine_angle(double X, double Y, double inv_h, float est)
+{
+    const int m = __float2int_rn(est * (float)kCircleInvStep) & (GC_CIRCLE_N - 1);
+    const double2 cs = __ldg(&kUnitCircle[m]);
+    const double t = fma(Y, cs.x, -X * cs.y) * inv_h;
+    const double t2 = t * t;
+    double p = fma(t2, 5.0 / 112.0, 3.0 / 40.0);
+    p = fma(t2, p, 1.0 / 6.0);
+    const double d = fma(t * t2, p, t);
+    return __dmul_rn((double)m, kCircleStep) + d;
+}
+
+// Polar and azimuthal angles of (x, y, z): theta in [0, pi] from the z axis, phi in
+// (-pi, 2 pi) (the caller folds negative values).
+__device__ __forceinline__ void polar_angles(float x, float y, float z, float rho, float, float,
+                                             float &theta, float &phi)
+{
+    theta = m_atan2(rho, z);
+    phi = m_atan2(y, x);
+}
+__device__ __forceinline__ void polar_angles(double x, double y, double z, double rho, double inv_rho,
+                                             double inv_r, double &theta, double &phi)
+{
+    theta = refine_angle(z, rho, inv_r, m_atan2((float)rho, (float)z));
+    phi = refine_angle(x, y, inv_rho, m_atan2((float)y, (float)x));
 }
 
 // ----------------------------------------------------------------------------------------
@@ -381,8 +418,8 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     const T r2 = rho2 + z * z;
     const T inv_rho = m_rsqrt(rho2), inv_r = m_rsqrt(r2);
     const T rho = rho2 * inv_rho, r = r2 * inv_r;
-    const T theta = m_atan2(rho, z);
-    T phi = m_atan2(y, x);
+    T theta, phi;
+    polar_angles(x, y, z, rho, inv_rho, inv_r, theta, phi);
     if (phi < T(0))
         phi += two_pi<T>();
     T xr = (r - gm.r_min) * gm.inv_dr;
