@@ -29,6 +29,8 @@ unless phi1_v is set. All draws come from numpy's PCG64 with the given seed.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -123,15 +125,18 @@ def potential_of(spec: WindSpec, phi1_v: float, gamma_p: float = 1.2) -> np.ndar
     return phi1_v * (AU / r) ** (2.0 * (gamma_p - 1.0))
 
 
-def wind_grid(spec: WindSpec, dtype=np.float32) -> np.ndarray:
-    """Node array [n_ph][n_th][n_r][8] of the synthetic wind (see module doc)."""
+def wind_grid(spec: WindSpec, dtype=np.float32, workers: int | None = None) -> np.ndarray:
+    """Node array [n_ph][n_th][n_r][8] of the synthetic wind (see module doc). The phi slabs
+    are independent and computed on `workers` threads (default: the host's cores, at most
+    16); every slab runs the same arithmetic, so the array does not depend on the count."""
     r = (spec.r_min_au + spec.dr_au * np.arange(spec.n_r)) * AU
     th = np.pi * np.arange(spec.n_th) / (spec.n_th - 1)
     ph = 2.0 * np.pi * np.arange(spec.n_ph) / spec.n_ph
     modes = perturbation_modes(spec)
     out = np.empty((spec.n_ph, spec.n_th, spec.n_r, 8), dtype=dtype)
     T, Rr = np.meshgrid(th, r, indexing="ij")  # (n_th, n_r)
-    for k in range(spec.n_ph):
+
+    def slab(k):
         X = np.stack([Rr * np.sin(T) * np.cos(ph[k]), Rr * np.sin(T) * np.sin(ph[k]),
                       Rr * np.cos(T)], -1)
         # exact poles: sin(pi) is not 0 in floating point
@@ -145,6 +150,15 @@ def wind_grid(spec: WindSpec, dtype=np.float32) -> np.ndarray:
             out[k, :, :, 7] = spec.phi1_v * (AU / Rr) ** (2.0 * (spec.gamma_p - 1.0))
         else:
             out[k, :, :, 7] = 0.0
+
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1)
+    if workers <= 1:
+        for k in range(spec.n_ph):
+            slab(k)
+    else:
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(slab, range(spec.n_ph)))
     return out
 
 

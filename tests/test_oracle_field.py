@@ -221,3 +221,10 @@ def test_synth_grid_matches_wind_at_nodes():
     np.testing.assert_allclose(g[5, 2, 3, 0:3], B[0], rtol=1e-12)
     np.testing.assert_allclose(g[5, 2, 3, 3:6], E[0], rtol=1e-12)
     np.testing.assert_allclose(g[5, 2, 3, 6], np.linalg.norm(B[0]), rtol=1e-12)
+
+
+def test_synth_grid_is_the_same_on_any_number_of_threads():
+    spec = synth.WindSpec(n_r=24, n_th=10, n_ph=20, eps=0.2, n_modes=6, phi1_v=500.0)
+    serial = synth.wind_grid(spec, dtype=np.float64, workers=1)
+    for w in (2, 7):
+        np.testing.assert_array_equal(synth.wind_grid(spec, dtype=np.float64, workers=w), serial)
