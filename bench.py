@@ -65,6 +65,11 @@ SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_p
 # rows through three 256 x 256 layers and the 256 x 8 output layer, FMA = 2 flop)
 NEURAL_FLOP_PER_EVAL = 3 * 4 * 256 * 256 * 2 + 4 * 256 * 8 * 2
 NEURAL_STEPS_PER_CALL = 10
+# SIREN parameters: BF16 hidden and output weights (3 x 256 x 256 + 8 x 256), FP32 first-layer
+# weights and biases (256 x 3 + 4 x 256 + 8)
+NETWORK_BYTES = 2 * (3 * 65536 + 2048) + 4 * (768 + 4 * 256 + 8)
+# timed advance calls per path on the large workload (after one warm-up call)
+LARGE_CALLS = 2
 
 
 def workload(n_per_lambda: int = 1_000_000):
@@ -221,12 +226,67 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _fit_siren(c, w, X, schedule):
+    """Train the context's SIREN on X["n_samples"] uniform-in-volume samples of its loaded
+    grid with the given (epochs, Adam step) schedule; returns the per-epoch losses and the
+    seconds taken."""
+    import torch
+
+    xs = torch.from_numpy(synth.siren_samples(X["n_samples"], w)).to("cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = [c.field_fit(xs, n_epochs=ep, batch=X["batch"], lr=lr) for ep, lr in schedule]
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    del xs
+    return np.concatenate(losses), t_fit
+
+
+def _siren_error(c, w):
+    """RMS error of the network against the grid interpolant on 2^20 held-out points, relative
+    to the RMS of the (scaled) channel groups B, E and |B|."""
+    import torch
+
+    xv = torch.from_numpy(synth.siren_samples(1 << 20, w, seed=1)).to("cuda")
+    y = torch.empty((xv.shape[0], 8), device="cuda")
+    t = torch.empty((xv.shape[0], 8), device="cuda")
+    c.siren_eval(xv, y)
+    c.field_targets(xv, t)
+    torch.cuda.synchronize()
+    d = (y - t).double()
+    return {g: float(torch.sqrt((d[:, sl] ** 2).mean() / (t[:, sl].double() ** 2).mean()))
+            for g, sl in (("B", slice(0, 3)), ("E", slice(3, 6)), ("absB", slice(6, 7)))}
+
+
+def _training_dict(X, schedule, loss, t_fit):
+    n_ep = sum(ep for ep, _ in schedule)
+    return {"samples": X["n_samples"], "epochs": n_ep, "batch": X["batch"],
+            "schedule": [[ep, lr] for ep, lr in schedule],
+            "seconds": t_fit, "samples_per_s": X["n_samples"] * n_ep / t_fit,
+            "loss_first_epoch": float(loss[0]) if len(loss) else None,
+            "loss_last_epoch": float(loss[-1]) if len(loss) else None}
+
+
+def _timed_calls(c, stream, dt, n_steps, n_calls):
+    """Device milliseconds of n_calls advance calls of n_steps each (CUDA events on the
+    context's stream)."""
+    import torch
+
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_calls):
+        c.advance(dt, n_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def neural_bench(args, nodes, local, stream, rank):
     """The neural-field path: train the SIREN on samples of the grid interpolant, measure its
     field error against the grid, then time the split-step push with the network as the
     field source (10^7 electrons)."""
-    import torch
-
     from paper_2403_06706_gb300 import gcpush, shard
 
     wn = synth.c4_neural(args.neural_particles)
@@ -238,41 +298,16 @@ def neural_bench(args, nodes, local, stream, rank):
     c.field_load(nodes, w.r_min_au, w.r_max_au)
     c.siren_set(synth.siren_init(seed=0), omega0=X["omega0"], r_max_au=w.r_max_au, B_scale=w.B1,
                 E_scale=w.B1 * w.u_sw)
-    xs = torch.from_numpy(synth.siren_samples(X["n_samples"], w)).to("cuda")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     schedule = X["schedule"] if args.neural_epochs is None else ((epochs, X["lr"]),)
-    losses = [c.field_fit(xs, n_epochs=ep, batch=X["batch"], lr=lr) for ep, lr in schedule]
-    loss = np.concatenate(losses)
-    torch.cuda.synchronize()
-    t_fit = time.perf_counter() - t0
-    del xs
-    # field error against the grid interpolant on held-out points (scaled channels)
-    xv = torch.from_numpy(synth.siren_samples(1 << 20, w, seed=1)).to("cuda")
-    y = torch.empty((xv.shape[0], 8), device="cuda")
-    t = torch.empty((xv.shape[0], 8), device="cuda")
-    c.siren_eval(xv, y)
-    c.field_targets(xv, t)
-    torch.cuda.synchronize()
-    d = (y - t).double()
-    err = {g: float(torch.sqrt((d[:, sl] ** 2).mean() / (t[:, sl].double() ** 2).mean()))
-           for g, sl in (("B", slice(0, 3)), ("E", slice(3, 6)), ("absB", slice(6, 7)))}
-    del xv, y, t, d
+    loss, t_fit = _fit_siren(c, w, X, schedule)
+    err = _siren_error(c, w)
     # push with the network as the field source
     c.field_select(gcpush.FIELD_SIREN)
     c.inject(list(wn.ensembles))
     for _ in range(args.warmup):
         c.advance(wn.dt, NEURAL_STEPS_PER_CALL)
-    torch.cuda.synchronize()
     s0 = c.stats()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        c.advance(wn.dt, NEURAL_STEPS_PER_CALL)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = _timed_calls(c, stream, wn.dt, NEURAL_STEPS_PER_CALL, args.steps)
     s1 = c.stats()
     n = wn.n_particles
     evals = s1["field_evals"] - s0["field_evals"]
@@ -289,15 +324,73 @@ def neural_bench(args, nodes, local, stream, rank):
                      "peak_basis": "measured bf16 cuBLAS, sustained (MEASURED_PEAKS.json)",
                      "flop_per_eval": NEURAL_FLOP_PER_EVAL, "evals": evals,
                      "eval_share_of_step": fms / ms},
-        "training": {"samples": X["n_samples"], "epochs": sum(ep for ep, _ in schedule), "batch": X["batch"],
-                     "schedule": [[ep, lr] for ep, lr in schedule],
-                     "seconds": t_fit, "samples_per_s": X["n_samples"] * sum(ep for ep, _ in schedule) / t_fit,
-                     "loss_first_epoch": float(loss[0]) if len(loss) else None,
-                     "loss_last_epoch": float(loss[-1]) if len(loss) else None},
+        "training": _training_dict(X, schedule, loss, t_fit),
         "field_rel_rms_vs_grid": err,
-        "footprint_bytes": {"network_bf16": 2 * (3 * 65536 + 2048) + 4 * (768 + 4 * 256 + 8),
-                            "grid_f32": int(nodes.nbytes)},
+        "footprint_bytes": {"network_bf16": NETWORK_BYTES, "grid_f32": int(nodes.nbytes)},
     }
+
+
+def large_bench(args, local, stream, rank):
+    """The large workload, grid against network: the 512x256x512 FP32 grid (2.15 GB; eps 0.2,
+    16 modes), 3x10^7 electrons with an E^-3 spectrum on [20, 500] keV, lambda 0.3 AU, tallies
+    of pitch x energy x r on 64 x 64 x 128 bins, pushed once with the inline grid gather and
+    once with a SIREN trained on this grid (the neural workload's schedule) as the field
+    source. Reports both rates, the network's field error against the grid and the two
+    footprints (the smoothness side of the comparison is tests/test_gpu_gain.py)."""
+    from paper_2403_06706_gb300 import gcpush, shard
+
+    wl = synth.c5_large(args.large_particles)
+    w = wl.wind
+    X = synth.c4_neural().extra
+    t0 = time.perf_counter()
+    nodes = synth.wind_grid(w, dtype=np.float32)
+    t_synth = time.perf_counter() - t0
+    tally = dict(cadence=100, n_mu=64, n_E=64, n_r=128, E_lo_keV=5.0, E_hi_keV=600.0,
+                 r_lo_au=w.r_min_au, r_hi_au=w.r_max_au)
+    n = wl.n_particles
+    out = {"workload": wl.name, "particles": n, "grid_synthesis_s": t_synth}
+
+    def context():
+        c = gcpush.Context(precision=gcpush.PREC_FP32_MIXED, device=local, stream=stream, seed=wl.seed,
+                           dt_init=wl.dt, id_base=shard.id_base(rank, n))
+        c.field_load(nodes, w.r_min_au, w.r_max_au)
+        return c
+
+    # the grid path: one warm-up launch, then LARGE_CALLS launches of PUSH_STEPS
+    c = context()
+    c.inject(list(wl.ensembles))
+    c.set_launch(**LAUNCH)
+    c.tally_arm(**tally)
+    c.advance(wl.dt, PUSH_STEPS)
+    ms = _timed_calls(c, stream, wl.dt, PUSH_STEPS, LARGE_CALLS)
+    t = c.tally_read()
+    out["grid"] = {"value": n * PUSH_STEPS * LARGE_CALLS / (ms / 1e3), "unit": UNIT,
+                   "push_steps": PUSH_STEPS * LARGE_CALLS, "warmup_push_steps": PUSH_STEPS,
+                   "tally_samples": int(t["n_seen"][0]), "tally_out_of_range": int(t["n_seen"][1])}
+    c.close()
+
+    # the neural path: the network trained on this grid, then the split-step push
+    c = context()
+    c.siren_set(synth.siren_init(seed=0), omega0=X["omega0"], r_max_au=w.r_max_au, B_scale=w.B1,
+                E_scale=w.B1 * w.u_sw)
+    loss, t_fit = _fit_siren(c, w, X, X["schedule"])
+    err = _siren_error(c, w)
+    c.field_select(gcpush.FIELD_SIREN)
+    c.inject(list(wl.ensembles))
+    c.tally_arm(**dict(tally, cadence=NEURAL_STEPS_PER_CALL))
+    c.advance(wl.dt, NEURAL_STEPS_PER_CALL)
+    ms = _timed_calls(c, stream, wl.dt, NEURAL_STEPS_PER_CALL, LARGE_CALLS)
+    t = c.tally_read()
+    out["neural"] = {"value": n * NEURAL_STEPS_PER_CALL * LARGE_CALLS / (ms / 1e3), "unit": UNIT,
+                     "push_steps": NEURAL_STEPS_PER_CALL * LARGE_CALLS,
+                     "warmup_push_steps": NEURAL_STEPS_PER_CALL,
+                     "tally_samples": int(t["n_seen"][0]), "tally_out_of_range": int(t["n_seen"][1]),
+                     "training": _training_dict(X, X["schedule"], loss, t_fit),
+                     "field_rel_rms_vs_grid": err}
+    c.close()
+    out["grid_over_neural"] = out["grid"]["value"] / out["neural"]["value"]
+    out["footprint_bytes"] = {"network_bf16": NETWORK_BYTES, "grid_f32": int(nodes.nbytes)}
+    return out
 
 
 def _measured_peaks() -> dict:
@@ -405,6 +498,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--neural-particles", type=int, default=10_000_000)
     ap.add_argument("--neural-epochs", type=int, default=None)
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large workload (512x256x512 grid against the network)")
+    ap.add_argument("--large-particles", type=int, default=30_000_000)
     ap.add_argument("--particles", type=int, default=3_000_000,
                     help="particles per GPU (split over the three lambda ensembles); smaller "
                          "values are for profiler captures")
@@ -609,6 +705,10 @@ def main():
     if not args.no_neural:
         neural = neural_bench(args, nodes, local, stream, rank)
 
+    large = None
+    if not args.no_large:
+        large = large_bench(args, local, stream, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, nodes)
@@ -623,7 +723,7 @@ def main():
             "parallelism": f"particles sharded by id, {world} GPU(s), no data-path collective",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clocks, "fp64_plain": fp64, "batched": batched, "variants": variants,
-            "neural": neural,
+            "neural": neural, "large": large,
             "accuracy": "FP32 path within 1e-4 of the FP64 oracle over the first 1e3 steps; "
                         "FP64 path within 1e-9 (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)",
         }
