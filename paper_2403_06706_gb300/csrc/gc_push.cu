@@ -497,7 +497,16 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
 #define GC_PUSH_F32_MIN_BLOCKS 4
 #endif
 constexpr int kMinBlocksF32 = GC_PUSH_F32_MIN_BLOCKS;
-constexpr int kMinBlocksF32TD = 3;
+// Time-dependent fields: 3 (4 spills 172 bytes and measured 6 % slower). Potential channel:
+// 4 like the steady kernel, with 84 bytes of spill (3 spill nothing but measured 5 % slower).
+#ifndef GC_PUSH_F32_TD_MIN_BLOCKS
+#define GC_PUSH_F32_TD_MIN_BLOCKS 3
+#endif
+constexpr int kMinBlocksF32TD = GC_PUSH_F32_TD_MIN_BLOCKS;
+#ifndef GC_PUSH_F32_POT_MIN_BLOCKS
+#define GC_PUSH_F32_POT_MIN_BLOCKS GC_PUSH_F32_MIN_BLOCKS
+#endif
+constexpr int kMinBlocksF32Pot = GC_PUSH_F32_POT_MIN_BLOCKS;
 // FP64: 2 (3 and 4 spill and measured 0.4 % and 1.7 % slower: the FP64 pipe, not
 // latency, bounds that kernel)
 #ifndef GC_PUSH_F64_MIN_BLOCKS
@@ -508,7 +517,7 @@ constexpr int kMinBlocksF64 = GC_PUSH_F64_MIN_BLOCKS;
 // Fused push: one thread owns a particle for all the steps of a launch and evaluates the
 // grid field inline (one copy of the evaluation serves all phases: instruction cache).
 template <typename T, bool TD, int POT>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : kMinBlocksF32) : kMinBlocksF64) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : (POT == POT_ON ? kMinBlocksF32Pot : kMinBlocksF32)) : kMinBlocksF64) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
                                                    const PushParams P)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
