@@ -60,6 +60,10 @@ PUSH_TRAFFIC_BYTES = 491_188_000 + 373_183_000
 # and 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / this count is its issue ceiling
 PUSH_THREAD_INSTR_PER_PSTEP = 1005
 PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
+# share of peak the FP64 push keeps its double-precision pipe busy (sm__pipe_fp64_cycles_active,
+# one ncu capture of the current kernel: profiles/push_kernel_fp64_parker256_300k.md); the
+# flop fraction counts a square root, reciprocal or arctangent as one flop and so reads lower
+FP64_PIPE_ACTIVE_NCU = 0.882
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 # Neural field: tensor-core work of one evaluation with its Jacobian (value + 3 tangent
 # rows through three 256 x 256 layers and the 256 x 8 output layer, FMA = 2 flop)
@@ -633,7 +637,8 @@ def main():
                 "note": "same workload, FP64 grid and arithmetic; timed after the same start-up",
                 "roofline": {"bound": "fp64", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": a64 / FP64_PEAK_TFLOPS, "flop_per_particle_step": FLOP_PER_PSTEP,
-                             "peak_basis": "nominal GB300 FP64 rate (no measured figure)"}}
+                             "peak_basis": "nominal GB300 FP64 rate (no measured figure)",
+                             "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE_NCU}}
         c64.close()
 
     # ---------------- 64 uneven ensembles, graph replay, autotuned launch shape -------------
