@@ -149,36 +149,63 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(wl, nodes, seconds=10.0):
-    """The FP64 oracle as it stands, on the host cores: the first 4096 ids of every
-    ensemble of the workload, advanced from injection for about `seconds`."""
+def _oracle_run(wl, nodes, n_per_ens, cores, seconds=None, n_steps=None, pilot_steps=50):
+    """Advance the first n_per_ens ids of every ensemble of `wl` with the FP64 oracle on
+    `cores` threads: `n_steps` steps from injection, or, after a pilot of `pilot_steps`, as
+    many as take about `seconds`. Returns (particles, timed steps, wall seconds)."""
     import oracle
     from oracle import AU
 
     f = oracle.grid_field(nodes, wl.wind.r_min_au * AU, wl.wind.r_max_au * AU)
     p = oracle.params(seed=wl.seed)
     oe = [oracle.ensemble(r0_au=e.r0_au, lat_deg=e.lat_deg, lon_deg=e.lon_deg, E0_keV=e.E0_keV,
-                          lam_au=e.lam_au, r_in_au=e.r_in, r_out_au=e.r_out_au) for e in wl.ensembles]
-    n_s = 4096
+                          lam_au=e.lam_au, r_in_au=e.r_in, r_out_au=e.r_out_au, energy_law=e.energy_law,
+                          E_lo_keV=e.E_lo_keV, E_hi_keV=e.E_hi_keV, E_index=e.E_index, mu_law=e.mu_law,
+                          scatter_law=e.scatter_law)
+          for e in wl.ensembles]
     first = np.cumsum([0] + [e.count for e in wl.ensembles])[:-1]
     parts = []
     for k, f0 in enumerate(first):
         counts = [0] * len(oe)
-        counts[k] = n_s
+        counts[k] = min(n_per_ens, wl.ensembles[k].count)
         parts.append(oracle.inject(f, p, oe, counts, id0=int(f0), dt=wl.dt))
     st = oracle.StateArrays({k: np.concatenate([q[k] for q in parts], axis=-1) for k in parts[0].arrays})
+    k0 = 0
+    if n_steps is None:
+        t0 = time.perf_counter()
+        oracle.advance(f, p, oe, st, 0.0, 0, wl.dt, pilot_steps, n_threads=cores)
+        pilot = time.perf_counter() - t0
+        k0 = pilot_steps
+        n_steps = int(max(pilot_steps, min(40000, pilot_steps * seconds / max(pilot, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.advance(f, p, oe, st, k0 * wl.dt, k0, wl.dt, n_steps, n_threads=cores)
+    return st.n, n_steps, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, nodes, seconds=10.0):
+    """The FP64 oracle as it stands, on the host cores: the first 4096 ids of every
+    ensemble of the workload, advanced for about `seconds` after 50 steps from injection; the
+    same sample on one core; and the plain 64x32x64 FP64 workload (4096 electrons, 3600
+    steps) in full on all cores, and for about five seconds on one core."""
     cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    oracle.advance(f, p, oe, st, 0.0, 0, wl.dt, 50, n_threads=cores)
-    pilot = time.perf_counter() - t0
-    n_steps = int(max(50, min(40000, 50 * seconds / max(pilot, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.advance(f, p, oe, st, 50 * wl.dt, 50, wl.dt, n_steps, n_threads=cores)
-    el = time.perf_counter() - t0
-    return {"value": st.n * n_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{st.n} particles (first {n_s} ids of each lambda ensemble) x {n_steps} "
-                      f"steps after 50 from injection, FP64 oracle on the same FP32 grid values, "
-                      f"{el:.1f} s wall"}
+    n, k, el = _oracle_run(wl, nodes, 4096, cores, seconds=seconds)
+    out = {"value": n * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} particles (first 4096 ids of each lambda ensemble) x {k} "
+                     f"steps after 50 from injection, FP64 oracle on the same FP32 grid values, "
+                     f"{el:.1f} s wall"}
+    n, k, el = _oracle_run(wl, nodes, 4096, 1, seconds=seconds / 2)
+    out["single_core"] = {"value": n * k / el, "unit": UNIT, "cores": 1,
+                          "sample": f"the same {n} particles x {k} steps after 50, {el:.1f} s wall"}
+    w1 = synth.c1_plain_fp64()
+    nodes1 = synth.wind_grid(w1.wind, dtype=np.float64)
+    n, k, el = _oracle_run(w1, nodes1, w1.n_particles, cores, n_steps=w1.n_steps)
+    n1, k1, el1 = _oracle_run(w1, nodes1, w1.n_particles, 1, seconds=5.0)
+    out["plain_fp64_workload"] = {
+        "workload": w1.name, "value": n * k / el, "unit": UNIT, "cores": cores,
+        "sample": f"in full: {n} particles x {k} steps from injection, {el:.1f} s wall",
+        "single_core": {"value": n1 * k1 / el1, "unit": UNIT, "cores": 1,
+                        "sample": f"{n1} particles x {k1} steps after 50 from injection, {el1:.1f} s wall"}}
+    return out
 
 
 def run_reference(args, rank, world):
