@@ -149,10 +149,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _oracle_run(wl, nodes, n_per_ens, cores, seconds=None, n_steps=None, pilot_steps=50):
-    """Advance the first n_per_ens ids of every ensemble of `wl` with the FP64 oracle on
-    `cores` threads: `n_steps` steps from injection, or, after a pilot of `pilot_steps`, as
-    many as take about `seconds`. Returns (particles, timed steps, wall seconds)."""
+def _oracle_setup(wl, nodes, n_per_ens):
+    """The FP64 oracle's field, parameters, ensembles and the injected state of the first
+    n_per_ens ids of every ensemble of `wl` (the ids the GPU path gives them)."""
     import oracle
     from oracle import AU
 
@@ -170,6 +169,16 @@ def _oracle_run(wl, nodes, n_per_ens, cores, seconds=None, n_steps=None, pilot_s
         counts[k] = min(n_per_ens, wl.ensembles[k].count)
         parts.append(oracle.inject(f, p, oe, counts, id0=int(f0), dt=wl.dt))
     st = oracle.StateArrays({k: np.concatenate([q[k] for q in parts], axis=-1) for k in parts[0].arrays})
+    return f, p, oe, st
+
+
+def _oracle_run(wl, nodes, n_per_ens, cores, seconds=None, n_steps=None, pilot_steps=50):
+    """Advance the first n_per_ens ids of every ensemble of `wl` with the FP64 oracle on
+    `cores` threads: `n_steps` steps from injection, or, after a pilot of `pilot_steps`, as
+    many as take about `seconds`. Returns (particles, timed steps, wall seconds)."""
+    import oracle
+
+    f, p, oe, st = _oracle_setup(wl, nodes, n_per_ens)
     k0 = 0
     if n_steps is None:
         t0 = time.perf_counter()
@@ -213,22 +222,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    from oracle import AU
 
     wl = workload()
     nodes = synth.wind_grid(wl.wind, dtype=np.float32)
-    f = oracle.grid_field(nodes, wl.wind.r_min_au * AU, wl.wind.r_max_au * AU)
-    p = oracle.params(seed=wl.seed)
-    oe = [oracle.ensemble(r0_au=e.r0_au, lat_deg=e.lat_deg, lon_deg=e.lon_deg, E0_keV=e.E0_keV,
-                          lam_au=e.lam_au, r_in_au=e.r_in, r_out_au=e.r_out_au) for e in wl.ensembles]
-    n_s = 512
-    first = np.cumsum([0] + [e.count for e in wl.ensembles])[:-1]
-    parts = []
-    for k, f0 in enumerate(first):
-        counts = [0] * len(oe)
-        counts[k] = n_s
-        parts.append(oracle.inject(f, p, oe, counts, id0=int(f0), dt=wl.dt))
-    st = oracle.StateArrays({k: np.concatenate([q[k] for q in parts], axis=-1) for k in parts[0].arrays})
+    f, p, oe, st = _oracle_setup(wl, nodes, 512)
     cores = os.cpu_count() or 1
     ref_steps = 2000  # push steps per bench step of this arm
     t, k = 0.0, 0
