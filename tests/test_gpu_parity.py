@@ -77,24 +77,34 @@ def test_fp64_matches_oracle(nodes64):
     assert rel < 1e-9
 
 
-def test_fp64_angles_at_the_poles_and_the_azimuth_seam(nodes64):
-    """Electrons started 1.5 degrees from either pole (the polar angle's first and last
-    cells), and 0.3 degrees past phi = pi and phi = 0, from where the Parker spiral carries
-    them across (where the FP32 estimate of phi jumps from pi to -pi, and where phi wraps
-    from 2 pi to 0), with short mean free paths: the FP64 polar angles, which are refined
-    from an FP32 estimate, give the oracle's library-atan2 result to 1e-9."""
-    ens = (synth.EnsembleSpec(40, r0_au=0.6, lat_deg=88.5, lon_deg=30.0, lam_au=0.05, r_out_au=R_OUT),
-           synth.EnsembleSpec(40, r0_au=0.6, lat_deg=-88.5, lon_deg=250.0, lam_au=0.05, r_out_au=R_OUT),
-           synth.EnsembleSpec(40, r0_au=0.6, lat_deg=3.0, lon_deg=180.3, lam_au=0.05, r_out_au=R_OUT),
-           synth.EnsembleSpec(40, r0_au=0.6, lat_deg=-7.0, lon_deg=0.3, lam_au=0.05, r_out_au=R_OUT))
+# Electrons started 1.5 degrees from either pole (the polar angle's first and last cells),
+# and 0.3 degrees past phi = pi and phi = 0, from where the Parker spiral carries them across
+# (where an FP32 estimate of phi jumps from pi to -pi, and where phi wraps from 2 pi to 0),
+# with short mean free paths.
+POLE_ENS = (synth.EnsembleSpec(40, r0_au=0.6, lat_deg=88.5, lon_deg=30.0, lam_au=0.05, r_out_au=R_OUT),
+            synth.EnsembleSpec(40, r0_au=0.6, lat_deg=-88.5, lon_deg=250.0, lam_au=0.05, r_out_au=R_OUT),
+            synth.EnsembleSpec(40, r0_au=0.6, lat_deg=3.0, lon_deg=180.3, lam_au=0.05, r_out_au=R_OUT),
+            synth.EnsembleSpec(40, r0_au=0.6, lat_deg=-7.0, lon_deg=0.3, lam_au=0.05, r_out_au=R_OUT))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_angles_at_the_poles_and_the_azimuth_seams(nodes64, nodes32, precision):
+    """FP64: the polar angles, refined from an FP32 estimate, give the oracle's library-atan2
+    result to 1e-9. FP32: the fast atan2 holds the 1e-4 bound at the same sites."""
     calls = [(0.5, 400, 0.0)]
-    g, _, gs = run_gpu(nodes64, WIND, ens, calls, gcpush.PREC_FP64, seed=5)
-    o, _, os_ = run_oracle(nodes64, WIND, ens, calls, seed=5)
-    _ints_equal(g, o)
-    assert gs["collisions"] == os_[0] and os_[0] > 100
+    nodes = nodes64 if precision == "fp64" else nodes32
+    prec = gcpush.PREC_FP64 if precision == "fp64" else gcpush.PREC_FP32_MIXED
+    g, _, gs = run_gpu(nodes, WIND, POLE_ENS, calls, prec, seed=5)
+    o, _, os_ = run_oracle(nodes, WIND, POLE_ENS, calls, seed=5)
     phi = np.degrees(np.arctan2(o["y"], o["x"])) % 360.0
     assert ((phi < 180.0) & (o["ens"] == 2)).sum() > 20 and ((phi > 300.0) & (o["ens"] == 3)).sum() > 20
-    err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes64, WIND, ens))
+    assert os_[0] > 100
+    if precision == "fp32":
+        _fp32_check(g, o, nodes, POLE_ENS)
+        return
+    _ints_equal(g, o)
+    assert gs["collisions"] == os_[0]
+    err = compare_states(g, o.arrays, 1e-9, momentum_scale(o, nodes, WIND, POLE_ENS))
     for k, v in err.items():
         assert v < 1e-9, (k, v, err)
 
