@@ -83,8 +83,10 @@ __device__ __forceinline__ void agg_inc64(unsigned long long *base, int idx)
 // Snapshot sample of one particle (Sect. 3). FP64: the bins are computed with the same
 // operations as the definition (double); FP32: the same formulas in float, with
 // gamma - 1 formed without cancellation.
+// Out of line: it runs once every cadence steps, and inlined its FP64 bin arithmetic would
+// hold registers the step loop needs.
 template <typename T>
-__device__ __forceinline__ void tally_sample(const TallyDev &T_, const PushParams &P, const Phys<T> &ph,
+__device__ __noinline__ void tally_sample(const TallyDev &T_, const PushParams &P, const Phys<T> &ph,
                                              uint32_t e, T x, T y, T z, T u, T mub, T Bm, double age,
                                              uint32_t ncoll, bool take)
 {
@@ -172,14 +174,21 @@ struct PState {
     uint32_t event, ncoll, flags;
 };
 
-// constants of one particle during a launch
+// constants of one particle that the step loop reads every step; the rest of its ensemble's
+// constants are read from the table where an event needs them
 struct PConst {
-    const EnsDev *E;
-    double lambda, r_in, r_out;
-    float ri2, ro2, lambda_f;
-    int scatter_law;
-    uint32_t id, e;
+    float ri2, ro2;
+    uint32_t e;
 };
+
+__device__ __forceinline__ double lambda_of(const PushParams &P, const EnsDev &E)
+{
+    return P.lambda_override > 0.0 ? P.lambda_override : E.lambda;
+}
+__device__ __forceinline__ float lambda_f_of(const PushParams &P, const EnsDev &E)
+{
+    return P.lambda_override > 0.0 ? (float)P.lambda_override : E.lambda_f;
+}
 
 // predictor / corrector weights of one step
 template <typename T>
@@ -193,15 +202,8 @@ __device__ __forceinline__ void load_particle(const PushParams &P, int64_t i, PC
     using Acc = AccOf<T>;
     const int64_t cap = P.st.cap;
     c.e = P.st.ens[i];
-    c.E = &P.ens[c.e];
-    c.lambda = P.lambda_override > 0.0 ? P.lambda_override : c.E->lambda;
-    c.r_in = c.E->r_in;
-    c.r_out = c.E->r_out;
-    c.ri2 = c.E->r_in2;
-    c.ro2 = c.E->r_out2;
-    c.lambda_f = P.lambda_override > 0.0 ? (float)P.lambda_override : c.E->lambda_f;
-    c.scatter_law = c.E->scatter_law;
-    c.id = P.st.id[i];
+    c.ri2 = P.ens[c.e].r_in2;
+    c.ro2 = P.ens[c.e].r_out2;
     s.Rx = Acc::from(P.st.x[i]);
     s.Ry = Acc::from(P.st.y[i]);
     s.Rz = Acc::from(P.st.z[i]);
@@ -329,6 +331,117 @@ __device__ __forceinline__ void phase_point(int phase, const PState<T> &s, const
 // Use the field evaluation Fo (with ax) of phase `phase` for particle slot i; after phase 1
 // a rebirth or a collision sets n_phase = 4. kk: index of the step's end time (t_birth on
 // rebirth).
+// The state a rebirth or a collision changes.
+template <typename T>
+struct RareState {
+    typename AccOf<T>::A Rx, Ry, Rz, U, S;
+    T mub;
+    double t_birth;
+    uint32_t event, ncoll;
+};
+
+// A rebirth (Sect. 3) or, if not reborn, a collision (Sect. 2.3) of particle slot i, with B
+// magnitude Bm_ and direction (b0, b1, b2) at the new position. Out of line: events are rare,
+// and inlined, their FP64 and Philox arithmetic holds registers the step loop needs (the
+// ensemble's constants are read from its table here for the same reason).
+template <typename T>
+__device__ __noinline__ RareState<T> rare_event(const PushParams &P, const Phys<T> &ph, int64_t i, bool reborn,
+                                                RareState<T> s, T Bm_, T b0, T b1, T b2, double t0,
+                                                long long kk)
+{
+    using Acc = AccOf<T>;
+    const EnsDev &E = P.ens[P.st.ens[i]];
+    const uint32_t id = P.st.id[i];
+    if (reborn) {
+        // Sect. 3: reborn at the injection site with the initial velocity
+        const uint4 wd = draw(id, P.seed, s.event++);
+        if constexpr (sizeof(T) == 8) {
+            s.Rx = E.R0[0];
+            s.Ry = E.R0[1];
+            s.Rz = E.R0[2];
+            s.S = -lambda_of(P, E) * log(u53(wd.z, wd.w));
+        } else {
+            s.Rx = df{E.R0_hi[0], E.R0_lo[0]};
+            s.Ry = df{E.R0_hi[1], E.R0_lo[1]};
+            s.Rz = df{E.R0_hi[2], E.R0_lo[2]};
+            s.S = df{lambda_f_of(P, E) * neg_log_u(u31(wd.z)), 0.0f};
+        }
+        s.U = Acc::from(P.st.u_inj[i]);
+        s.mub = (T)P.st.mub_inj[i];
+        s.ncoll = 0;
+        s.t_birth = step_time(t0, kk, P.dt);
+    } else {
+        // inertial-frame elastic collision: |p| kept, B at R^{n+1}; new pitch
+        // cosine from Eq. 10 (mu = 1 - 2a) or Eq. 12 (mu = +-sqrt(a))
+        const uint4 wd = draw(id, P.seed, s.event++);
+        if constexpr (sizeof(T) == 8) {
+            const double a = u53(wd.x, wd.y);
+            const double mu_new = (E.scatter_law == 0) ? 1.0 - 2.0 * a : ((wd.x & 1u) ? -sqrt(a) : sqrt(a));
+            const double Bm = (double)Bm_;
+            const double uu = Acc::to(s.U);
+            if (P.wind_u > 0.0) {
+                // Sect. 3.2: elastic in the frame of the wind u = wind_u R/r; the guiding
+                // centre drifts with u_perp already, so the frame change is a boost along
+                // b by V = u.b (p_perp unchanged): u~ = gV (u - V gamma), back with -V
+                const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
+                const double V = P.wind_u * (X * b0 + Y * b1 + Z * b2) /
+                                 sqrt(X * X + Y * Y + Z * Z);
+                const double gV = 1.0 / sqrt(1.0 - V * V / P.c2);
+                const double pp2 = 2.0 * (double)s.mub * Bm / P.m;
+                const double gam = sqrt(1.0 + (uu * uu + pp2) / P.c2);
+                const double ut = gV * (uu - V * gam);
+                const double pt2 = ut * ut + pp2;
+                const double gt = sqrt(1.0 + pt2 / P.c2);
+                s.U = gV * (mu_new * sqrt(pt2) + V * gt);
+                s.mub = (1.0 - mu_new * mu_new) * pt2 * P.m / (2.0 * Bm);
+            } else {
+                const double pm2 = uu * uu + 2.0 * (double)s.mub * Bm / P.m;
+                const double pm = sqrt(pm2);
+                s.U = mu_new * pm;
+                s.mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
+            }
+            if (P.collision_form == 0)
+                s.S = -lambda_of(P, E) * log(u53(wd.z, wd.w));
+        } else {
+            // sin^2 of the new pitch angle without cancellation: 4 a (1 - a)
+            // for Eq. 10 (mu = (1 - a) - a), 1 - a for Eq. 12 (mu^2 = a)
+            const UPair ua = u31(wd.x);
+            float mu_new, sin2;
+            if (E.scatter_law == 0) {
+                mu_new = ua.ub - ua.u;
+                sin2 = 4.0f * ua.u * ua.ub;
+            } else {
+                mu_new = (wd.x & 1u) ? -sqrtf(ua.u) : sqrtf(ua.u);
+                sin2 = ua.ub;
+            }
+            const float Bm = (float)Bm_;
+            const float uu = (float)Acc::val(s.U);
+            const float pp2 = 2.0f * (float)s.mub * Bm * (float)ph.inv_m;
+            float pm2 = uu * uu + pp2;
+            if (P.wind_u > 0.0) {
+                // the wind-frame collision of the FP64 branch above, in float
+                const float X = Acc::val(s.Rx), Y = Acc::val(s.Ry), Z = Acc::val(s.Rz);
+                const float V = (float)P.wind_u * (X * b0 + Y * b1 + Z * b2) *
+                                rsqrtf(X * X + Y * Y + Z * Z);
+                const float ic2 = (float)ph.inv_c2;
+                const float gV = rsqrtf(1.0f - V * V * ic2);
+                const float gam = sqrtf(1.0f + pm2 * ic2);
+                const float ut = gV * (uu - V * gam);
+                pm2 = ut * ut + pp2;
+                const float gt = sqrtf(1.0f + pm2 * ic2);
+                s.U = df{gV * (mu_new * sqrtf(pm2) + V * gt), 0.0f};
+            } else {
+                s.U = df{mu_new * sqrtf(pm2), 0.0f};
+            }
+            s.mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
+            if (P.collision_form == 0)
+                s.S = df{lambda_f_of(P, E) * neg_log_u(u31(wd.z)), 0.0f};
+        }
+        ++s.ncoll;
+    }
+    return s;
+}
+
 template <typename T>
 __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i, PState<T> &s, const PConst &c,
                                               const T Fo[4],
@@ -353,11 +466,11 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
                 collide = Acc::nonpos(s.S);
             } else {
                 // the per-step draw of Eq. 9: collide if a < 1 - exp(-ds / lambda)
-                const uint4 wd = draw(c.id, P.seed, s.event++);
+                const uint4 wd = draw(P.st.id[i], P.seed, s.event++);
                 if constexpr (sizeof(T) == 8)
-                    collide = u53(wd.x, wd.y) < 1.0 - exp(-(double)ds / c.lambda);
+                    collide = u53(wd.x, wd.y) < 1.0 - exp(-(double)ds / lambda_of(P, P.ens[c.e]));
                 else
-                    collide = u31(wd.x).u < -expm1f(-(float)ds / c.lambda_f);
+                    collide = u31(wd.x).u < -expm1f(-(float)ds / lambda_f_of(P, P.ens[c.e]));
             }
         }
         bool reborn = false;
@@ -365,7 +478,7 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
             if (sizeof(T) == 8) {
                 const double xx = Acc::to(s.Rx), yy = Acc::to(s.Ry), zz = Acc::to(s.Rz);
                 const double r1 = sqrt(xx * xx + yy * yy + zz * zz);
-                reborn = (r1 < c.r_in || r1 > c.r_out);
+                reborn = (r1 < P.ens[c.e].r_in || r1 > P.ens[c.e].r_out);
             } else {
                 const float xx = (float)px, yy = (float)py, zz = (float)pz;
                 const float r2 = xx * xx + yy * yy + zz * zz;
@@ -373,101 +486,21 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
                     // near the shell: decide in double from the accumulated position
                     const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
                     const double r1 = sqrt(X * X + Y * Y + Z * Z);
-                    reborn = (r1 < c.r_in || r1 > c.r_out);
+                    reborn = (r1 < P.ens[c.e].r_in || r1 > P.ens[c.e].r_out);
                 } else {
                     reborn = (r2 < c.ri2 || r2 > c.ro2);
                 }
             }
         }
-        if (reborn) {
-            // Sect. 3: reborn at the injection site with the initial velocity
-            const uint4 wd = draw(c.id, P.seed, s.event++);
-            if constexpr (sizeof(T) == 8) {
-                s.Rx = c.E->R0[0];
-                s.Ry = c.E->R0[1];
-                s.Rz = c.E->R0[2];
-                s.S = -c.lambda * log(u53(wd.z, wd.w));
-            } else {
-                s.Rx = df{c.E->R0_hi[0], c.E->R0_lo[0]};
-                s.Ry = df{c.E->R0_hi[1], c.E->R0_lo[1]};
-                s.Rz = df{c.E->R0_hi[2], c.E->R0_lo[2]};
-                s.S = df{c.lambda_f * neg_log_u(u31(wd.z)), 0.0f};
-            }
-            s.U = Acc::from(P.st.u_inj[i]);
-            s.mub = (T)P.st.mub_inj[i];
-            s.ncoll = 0;
-            s.t_birth = step_time(t0, kk, P.dt);
-            ++n_reb;
-            n_phase = 4;
-        } else if (collide) {
-            // inertial-frame elastic collision: |p| kept, B at R^{n+1}; new pitch
-            // cosine from Eq. 10 (mu = 1 - 2a) or Eq. 12 (mu = +-sqrt(a))
-            const uint4 wd = draw(c.id, P.seed, s.event++);
-            if constexpr (sizeof(T) == 8) {
-                const double a = u53(wd.x, wd.y);
-                const double mu_new = (c.scatter_law == 0) ? 1.0 - 2.0 * a : ((wd.x & 1u) ? -sqrt(a) : sqrt(a));
-                const double Bm = (double)ax.Bm;
-                const double uu = Acc::to(s.U);
-                if (P.wind_u > 0.0) {
-                    // Sect. 3.2: elastic in the frame of the wind u = wind_u R/r; the guiding
-                    // centre drifts with u_perp already, so the frame change is a boost along
-                    // b by V = u.b (p_perp unchanged): u~ = gV (u - V gamma), back with -V
-                    const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
-                    const double V = P.wind_u * (X * ax.b[0] + Y * ax.b[1] + Z * ax.b[2]) /
-                                     sqrt(X * X + Y * Y + Z * Z);
-                    const double gV = 1.0 / sqrt(1.0 - V * V / P.c2);
-                    const double pp2 = 2.0 * (double)s.mub * Bm / P.m;
-                    const double gam = sqrt(1.0 + (uu * uu + pp2) / P.c2);
-                    const double ut = gV * (uu - V * gam);
-                    const double pt2 = ut * ut + pp2;
-                    const double gt = sqrt(1.0 + pt2 / P.c2);
-                    s.U = gV * (mu_new * sqrt(pt2) + V * gt);
-                    s.mub = (1.0 - mu_new * mu_new) * pt2 * P.m / (2.0 * Bm);
-                } else {
-                    const double pm2 = uu * uu + 2.0 * (double)s.mub * Bm / P.m;
-                    const double pm = sqrt(pm2);
-                    s.U = mu_new * pm;
-                    s.mub = (1.0 - mu_new * mu_new) * pm2 * P.m / (2.0 * Bm);
-                }
-                if (P.collision_form == 0)
-                    s.S = -c.lambda * log(u53(wd.z, wd.w));
-            } else {
-                // sin^2 of the new pitch angle without cancellation: 4 a (1 - a)
-                // for Eq. 10 (mu = (1 - a) - a), 1 - a for Eq. 12 (mu^2 = a)
-                const UPair ua = u31(wd.x);
-                float mu_new, sin2;
-                if (c.scatter_law == 0) {
-                    mu_new = ua.ub - ua.u;
-                    sin2 = 4.0f * ua.u * ua.ub;
-                } else {
-                    mu_new = (wd.x & 1u) ? -sqrtf(ua.u) : sqrtf(ua.u);
-                    sin2 = ua.ub;
-                }
-                const float Bm = (float)ax.Bm;
-                const float uu = (float)Acc::val(s.U);
-                const float pp2 = 2.0f * (float)s.mub * Bm * (float)ph.inv_m;
-                float pm2 = uu * uu + pp2;
-                if (P.wind_u > 0.0) {
-                    // the wind-frame collision of the FP64 branch above, in float
-                    const float X = Acc::val(s.Rx), Y = Acc::val(s.Ry), Z = Acc::val(s.Rz);
-                    const float V = (float)P.wind_u * (X * ax.b[0] + Y * ax.b[1] + Z * ax.b[2]) *
-                                    rsqrtf(X * X + Y * Y + Z * Z);
-                    const float ic2 = (float)ph.inv_c2;
-                    const float gV = rsqrtf(1.0f - V * V * ic2);
-                    const float gam = sqrtf(1.0f + pm2 * ic2);
-                    const float ut = gV * (uu - V * gam);
-                    pm2 = ut * ut + pp2;
-                    const float gt = sqrtf(1.0f + pm2 * ic2);
-                    s.U = df{gV * (mu_new * sqrtf(pm2) + V * gt), 0.0f};
-                } else {
-                    s.U = df{mu_new * sqrtf(pm2), 0.0f};
-                }
-                s.mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
-                if (P.collision_form == 0)
-                    s.S = df{c.lambda_f * neg_log_u(u31(wd.z)), 0.0f};
-            }
-            ++s.ncoll;
-            ++n_coll;
+        if (reborn || collide) {
+            RareState<T> o{s.Rx, s.Ry, s.Rz, s.U, s.S, s.mub, s.t_birth, s.event, s.ncoll};
+            o = rare_event<T>(P, ph, i, reborn, o, ax.Bm, ax.b[0], ax.b[1], ax.b[2], t0, kk);
+            s.Rx = o.Rx; s.Ry = o.Ry; s.Rz = o.Rz; s.U = o.U; s.S = o.S;
+            s.mub = o.mub; s.t_birth = o.t_birth; s.event = o.event; s.ncoll = o.ncoll;
+            if (reborn)
+                ++n_reb;
+            else
+                ++n_coll;
             n_phase = 4;
         } else {
 #pragma unroll
@@ -517,8 +550,8 @@ constexpr int kMinBlocksF64 = GC_PUSH_F64_MIN_BLOCKS;
 // Fused push: one thread owns a particle for all the steps of a launch and evaluates the
 // grid field inline (one copy of the evaluation serves all phases: instruction cache).
 template <typename T, bool TD, int POT>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : (POT == POT_ON ? kMinBlocksF32Pot : kMinBlocksF32)) : kMinBlocksF64) push_kernel(const GridMeta<T> gm, const Phys<T> ph,
-                                                   const PushParams P)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : (POT == POT_ON ? kMinBlocksF32Pot : kMinBlocksF32)) : kMinBlocksF64) push_kernel(const GridMeta<T> gm, const __grid_constant__ Phys<T> ph,
+                                                   const __grid_constant__ PushParams P)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned n_coll = 0, n_reb = 0;
@@ -721,7 +754,7 @@ __device__ __forceinline__ void flush_counters(const PushParams &P, unsigned n_c
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(128) split_kernel(const Phys<float> ph, const SplitParams Q)
+__global__ void __launch_bounds__(128) split_kernel(const __grid_constant__ Phys<float> ph, const __grid_constant__ SplitParams Q)
 {
     using Acc = AccOf<float>;
     const PushParams &P = Q.P;
@@ -811,7 +844,7 @@ __global__ void __launch_bounds__(128) split_kernel(const Phys<float> ph, const 
         } else if constexpr (KIND == SPLIT_INJ_FIX) {
             // the injection's field-dependent part with this source: mu_B from |B| at the
             // site, F^n there, and the F^{n-1} request at X^n - dt F^n (Sect. 2.2)
-            const InjDraw d = inj_draw(*c.E, c.id, P.seed, P.m, P.c2);
+            const InjDraw d = inj_draw(P.ens[c.e], P.st.id[i], P.seed, P.m, P.c2);
             load_sample(Q.S, k, Q.g_in_sample, smp);
             s.flags |= smp.flags;
             const double Bm = (double)m_sqrt(dot3(smp.B, smp.B));
