@@ -523,6 +523,29 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
             s.F1[k] = Fo[k];
     }
 }
+// The start-up history after a rebirth or a collision (phases 2 and 3 of the fused push):
+// F^n at the new state and F^{n-1} at X^n - dt F^n. Out of line, like the events themselves,
+// so that the step loop carries only the two phases every step has.
+template <typename T>
+struct Restart {
+    T F0[4], F1[4], vpar0, Bm0;
+    uint32_t flags;
+};
+
+template <typename T, bool TD, int POT>
+__device__ __noinline__ Restart<T> restart_history(const GridMeta<T> &gm, const Phys<T> &ph, T x, T y, T z,
+                                                   T u, T mub, T dtT, T t_end)
+{
+    Restart<T> o;
+    Aux<T> ax;
+    o.flags = eval_F<T, TD, POT>(gm, ph, x, y, z, u, mub, o.F0, ax, t_end);
+    o.vpar0 = ax.vpar;
+    o.Bm0 = ax.Bm;
+    o.flags |= eval_F<T, TD, POT>(gm, ph, x - dtT * o.F0[0], y - dtT * o.F0[1], z - dtT * o.F0[2],
+                                  u - dtT * o.F0[3], mub, o.F1, ax, t_end - dtT);
+    return o;
+}
+
 // ----------------------------------------------------------------------------------------
 // Resident CTAs of 128 threads per SM the FP32 push is compiled for (register budget:
 // 65536 / (128 x blocks) per thread); the time-dependent variant carries more state.
@@ -530,8 +553,8 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
 #define GC_PUSH_F32_MIN_BLOCKS 4
 #endif
 constexpr int kMinBlocksF32 = GC_PUSH_F32_MIN_BLOCKS;
-// Time-dependent fields: 3 (4 spills 172 bytes and measured 6 % slower). Potential channel:
-// 4 like the steady kernel, with 84 bytes of spill (3 spill nothing but measured 5 % slower).
+// Time-dependent fields: 3 (4 spilled 172 bytes and measured 6 % slower). Potential channel:
+// 4 like the steady kernel (3 measured 5 % slower).
 #ifndef GC_PUSH_F32_TD_MIN_BLOCKS
 #define GC_PUSH_F32_TD_MIN_BLOCKS 3
 #endif
@@ -550,7 +573,7 @@ constexpr int kMinBlocksF64 = GC_PUSH_F64_MIN_BLOCKS;
 // Fused push: one thread owns a particle for all the steps of a launch and evaluates the
 // grid field inline (one copy of the evaluation serves all phases: instruction cache).
 template <typename T, bool TD, int POT>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : (POT == POT_ON ? kMinBlocksF32Pot : kMinBlocksF32)) : kMinBlocksF64) push_kernel(const GridMeta<T> gm, const __grid_constant__ Phys<T> ph,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : (POT == POT_ON ? kMinBlocksF32Pot : kMinBlocksF32)) : kMinBlocksF64) push_kernel(const __grid_constant__ GridMeta<T> gm, const __grid_constant__ Phys<T> ph,
                                                    const __grid_constant__ PushParams P)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -567,6 +590,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                          dtT * T(-1.0 / 12.0)};
     // time-dependent fields: time of the call's start after the first snapshot
     const T tr0 = TD ? (T)(t0 - gm.t_snap0) : T(0);
+    constexpr bool kRestartOutOfLine = POT != POT_ON;
 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.st.n; i += stride) {
         PConst c;
@@ -584,8 +608,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
             // the start-up's F^{n-1} one step earlier
             const T t_end = TD ? tr0 + (T)(P.kbase + k + 1) * dtT : T(0);
             int n_phase = 2;
+            // phase 0: predictor point and corrector; phase 1: F^{n+1}, free path, events;
+            // after an event, phases 2-3 restart the history: out of line, except in the
+            // potential-channel variant, where that measured slower (it spills there)
 #pragma unroll 1
-            for (int phase = 0; phase < n_phase; ++phase) {
+            for (int phase = 0; phase < (kRestartOutOfLine ? 2 : n_phase); ++phase) {
                 T px, py, pz, pu;
                 phase_point(phase, s, w, dtT, px, py, pz, pu);
                 T Fo[4];
@@ -594,6 +621,19 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                                               phase == 3 ? t_end - dtT : t_end);
                 phase_consume(phase, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, t0, (long long)(P.kbase + k + 1),
                               n_coll, n_reb);
+            }
+            if (kRestartOutOfLine && n_phase == 4) {
+                using Acc = AccOf<T>;
+                const Restart<T> o = restart_history<T, TD, POT>(gm, ph, Acc::val(s.Rx), Acc::val(s.Ry),
+                                                                 Acc::val(s.Rz), Acc::val(s.U), s.mub, dtT, t_end);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    s.F0[q] = o.F0[q];
+                    s.F1[q] = o.F1[q];
+                }
+                s.vpar0 = o.vpar0;
+                s.Bm0 = o.Bm0;
+                s.flags |= o.flags;
             }
             s.hprev = dtT;
             if (!(m_finite(AccOf<T>::val(s.Rx)) && m_finite(AccOf<T>::val(s.U)) && m_finite(s.F0[0])))
