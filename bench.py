@@ -55,11 +55,11 @@ FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300
 # DRAM bytes (read + write) of one push launch of the default workload (3x10^6 particles,
 # 1000 steps per launch), from one ncu capture of the current kernel
 # (profiles/push_kernel_fp32_parker256_3e6.md); reported only for that launch shape
-PUSH_TRAFFIC_BYTES = 491_188_000 + 373_183_000
+PUSH_TRAFFIC_BYTES = 492_272_000 + 372_708_000
 # thread instructions one particle-step of the FP32 push issues (smsp__inst_executed x
 # threads per warp instruction / particle-steps, same capture): the kernel is issue-bound,
 # and 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / this count is its issue ceiling
-PUSH_THREAD_INSTR_PER_PSTEP = 1005
+PUSH_THREAD_INSTR_PER_PSTEP = 980
 PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
 # share of peak the FP64 push keeps its double-precision pipe busy (sm__pipe_fp64_cycles_active,
 # one ncu capture of the current kernel: profiles/push_kernel_fp64_parker256_300k.md); the
