@@ -91,6 +91,16 @@ def test_table_is_the_unit_circle_at_the_reference_angles():
     assert cs[n // 4, 1] == 1.0 and cs[n // 2, 0] == -1.0 and cs[3 * n // 4, 1] == -1.0
 
 
+def test_fp32_atan_polynomial_meets_its_stated_bound():
+    """atan(t) ~ t p(t^2) on [0, 1] with the kernel's coefficients, evaluated exactly (float64):
+    within the 4e-8 the kernel's comment states, and exact at t = 0."""
+    c = np.array(_atan2_f32_coeffs(), dtype=np.float64)  # highest power first
+    t = np.linspace(0.0, 1.0, 400_001)
+    approx = t * np.polyval(c, t * t)
+    assert np.abs(approx - np.arctan(t)).max() < 4e-8
+    assert approx[0] == 0.0
+
+
 def test_fp32_estimate_is_within_the_refinements_margin():
     coeffs = _atan2_f32_coeffs()
     assert len(coeffs) == 8
