@@ -92,12 +92,13 @@ def test_table_is_the_unit_circle_at_the_reference_angles():
 
 
 def test_fp32_atan_polynomial_meets_its_stated_bound():
-    """atan(t) ~ t p(t^2) on [0, 1] with the kernel's coefficients, evaluated exactly (float64):
-    within the 4e-8 the kernel's comment states, and exact at t = 0."""
+    """atan(t) ~ t p(t^2) on [0, 1] with the kernel's float coefficients, evaluated in float64:
+    within the 7.1e-8 the kernel's comment states (4e-8 before the coefficients are rounded to
+    float), and exact at t = 0."""
     c = np.array(_atan2_f32_coeffs(), dtype=np.float64)  # highest power first
     t = np.linspace(0.0, 1.0, 400_001)
     approx = t * np.polyval(c, t * t)
-    assert np.abs(approx - np.arctan(t)).max() < 4e-8
+    assert np.abs(approx - np.arctan(t)).max() < 7.1e-8
     assert approx[0] == 0.0
 
 
