@@ -400,6 +400,8 @@ int enqueue_advance(gc_ctx *c, cudaStream_t s, double dt, int64_t n_steps, doubl
     P.seed = c->opt.seed;
     P.m = c->opt.mass;
     P.c2 = kC * kC;
+    P.two_over_m = 2.0 / c->opt.mass;
+    P.inv_c2 = 1.0 / (kC * kC);
     P.tally_on = c->tally_on ? 1 : 0;
     P.tally = c->tdev;
     P.gflags = c->d_flags;
@@ -640,6 +642,8 @@ gcp::SplitParams split_params(gc_ctx *c, double dt, double lambda_au)
     P.seed = c->opt.seed;
     P.m = c->opt.mass;
     P.c2 = kC * kC;
+    P.two_over_m = 2.0 / c->opt.mass;
+    P.inv_c2 = 1.0 / (kC * kC);
     P.tally_on = c->tally_on ? 1 : 0;
     P.tally = c->tdev;
     P.gflags = c->d_flags;

@@ -49,6 +49,7 @@ struct PushParams {
     uint32_t seed;
     int32_t tally_on;
     double m, c2;           // rest mass (kg), c^2
+    double two_over_m, inv_c2; // 2 / m and 1 / c^2 (the FP32 path's collision bookkeeping)
     TallyDev tally;
     uint32_t *gflags;              // OR of particle flags raised in this launch
     unsigned long long *counters;  // [0] collisions, [1] rebirths

@@ -11,7 +11,10 @@
 //
 // Precision: GC_PREC_FP64 runs everything in double. GC_PREC_FP32_MIXED evaluates the
 // field and Eqs. 1-2 in float and accumulates R, gamma v_par and the free path in
-// double-float pairs; the rare collision and rebirth updates run in double.
+// double-float pairs; mu_B is a double-float too (the right-hand side takes its float
+// part), and the rare collision and rebirth updates of gamma v_par and mu_B run in double.
+#include <type_traits>
+
 #include "gc_device.cuh"
 #include "gc_internal.h"
 
@@ -53,6 +56,45 @@ __device__ __forceinline__ UPair u31(uint32_t w)
 
 // -ln(u) without cancellation at either end of (0, 1)
 __device__ __forceinline__ float neg_log_u(UPair p) { return p.u < 0.5f ? -logf(p.u) : -log1pf(-p.ub); }
+
+// The same draw as a double pair (a, 1 - a): the member below 1/2 is taken from the float
+// that holds it without cancellation and the other is 1 minus it, so the two sum to 1 to
+// double rounding (the two floats of a UPair sum to 1 only to float rounding).
+struct UPairD {
+    double a, b;
+};
+
+__device__ __forceinline__ UPairD u31_d(UPair p)
+{
+    if (p.u < 0.5f) {
+        const double a = (double)p.u;
+        return {a, 1.0 - a};
+    }
+    const double b = (double)p.ub;
+    return {1.0 - b, b};
+}
+
+// FP64 reciprocal and square root by Newton's method from the float estimates, without the
+// FP64 division and square-root sequences (GB300's FP64 pipe runs at 1/64 of the FP32 rate,
+// and a warp with one colliding lane waits for them). For 0 < x < 3e38: the float estimate
+// has a relative error e0 < 2^-21, each Newton step squares it (y <- y + y (1 - x y) for 1/x,
+// y <- y + y (1 - x y^2) / 2 for 1/sqrt(x)), so two steps leave e0^4 < 2^-84 and the result
+// carries only the FP64 roundings of the steps, a few ulp.
+__device__ __forceinline__ double rcp_newton(double x)
+{
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+__device__ __forceinline__ double rsqrt_newton(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
+    return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+}
+
+__device__ __forceinline__ double sqrt_newton(double x) { return x > 0.0 ? x * rsqrt_newton(x) : 0.0; }
 
 // Time of the end of local step k. Out of line so that the FP64 arithmetic stays in the
 // rare branches that need it (rebirth, tally) instead of being hoisted into every step.
@@ -158,6 +200,32 @@ __device__ __noinline__ void tally_sample(const TallyDev &T_, const PushParams &
 }
 
 // ----------------------------------------------------------------------------------------
+// mu_B of the FP32 path is a double-float: the float the right-hand side takes and a low
+// part for the collision bookkeeping; the FP64 path has no low part.
+struct NoLo {
+};
+template <typename T>
+using MubLo = typename std::conditional<sizeof(T) == 4, float, NoLo>::type;
+
+template <typename T>
+__device__ __forceinline__ MubLo<T> mub_lo_of(double d, T hi)
+{
+    if constexpr (sizeof(T) == 4)
+        return (float)(d - (double)hi);
+    else
+        return NoLo{};
+}
+
+template <typename T>
+__device__ __forceinline__ double mub_value(T hi, MubLo<T> lo)
+{
+    if constexpr (sizeof(T) == 4)
+        return (double)hi + (double)lo;
+    else
+        return (double)hi;
+}
+
+// ----------------------------------------------------------------------------------------
 // Per-particle state and the four evaluation phases of a step, shared by the fused push
 // (field evaluated inline) and the split-step push (field samples from a buffer).
 //   phase 0  F* at the predictor point (Eq. 5), then the corrector (Eq. 6)
@@ -169,7 +237,9 @@ template <typename T>
 struct PState {
     using A = typename AccOf<T>::A;
     A Rx, Ry, Rz, U, S;
-    T mub, F0[4], F1[4], vpar0, hprev, Bm0;
+    T mub;
+    MubLo<T> mub_lo;
+    T F0[4], F1[4], vpar0, hprev, Bm0;
     double t_birth;
     uint32_t event, ncoll, flags;
 };
@@ -210,6 +280,7 @@ __device__ __forceinline__ void load_particle(const PushParams &P, int64_t i, PC
     s.U = Acc::from(P.st.u[i]);
     s.S = Acc::from(P.st.s_rem[i]);
     s.mub = (T)P.st.mub[i];
+    s.mub_lo = mub_lo_of<T>(P.st.mub[i], s.mub);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         s.F0[k] = (T)P.st.F0[k * cap + i];
@@ -234,7 +305,7 @@ __device__ __forceinline__ void store_particle(const PushParams &P, int64_t i, c
     P.st.z[i] = Acc::to(s.Rz);
     P.st.u[i] = Acc::to(s.U);
     P.st.s_rem[i] = Acc::to(s.S);
-    P.st.mub[i] = (double)s.mub;
+    P.st.mub[i] = mub_value<T>(s.mub, s.mub_lo);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         P.st.F0[k * cap + i] = (double)s.F0[k];
@@ -336,6 +407,7 @@ template <typename T>
 struct RareState {
     typename AccOf<T>::A Rx, Ry, Rz, U, S;
     T mub;
+    MubLo<T> mub_lo;
     double t_birth;
     uint32_t event, ncoll;
 };
@@ -368,6 +440,7 @@ __device__ __noinline__ RareState<T> rare_event(const PushParams &P, const Phys<
         }
         s.U = Acc::from(P.st.u_inj[i]);
         s.mub = (T)P.st.mub_inj[i];
+        s.mub_lo = mub_lo_of<T>(P.st.mub_inj[i], s.mub);
         s.ncoll = 0;
         s.t_birth = step_time(t0, kk, P.dt);
     } else {
@@ -403,37 +476,42 @@ __device__ __noinline__ RareState<T> rare_event(const PushParams &P, const Phys<
             if (P.collision_form == 0)
                 s.S = -lambda_of(P, E) * log(u53(wd.z, wd.w));
         } else {
-            // sin^2 of the new pitch angle without cancellation: 4 a (1 - a)
-            // for Eq. 10 (mu = (1 - a) - a), 1 - a for Eq. 12 (mu^2 = a)
-            const UPair ua = u31(wd.x);
-            float mu_new, sin2;
+            // FP32 path: the pitch is drawn from float uniforms, the momentum bookkeeping
+            // runs in FP64 on the double-float gamma v_par and mu_B, so |p| (|p~| in the wind
+            // frame) is kept to double-float rounding (~1e-14), not FP32's; mu^2 + sin^2 = 1
+            // to FP64 rounding (u31_d), and 1/x, sqrt(x) come from Newton steps.
+            const UPairD ua = u31_d(u31(wd.x));
+            double mu_new, sin2;
             if (E.scatter_law == 0) {
-                mu_new = ua.ub - ua.u;
-                sin2 = 4.0f * ua.u * ua.ub;
+                mu_new = ua.b - ua.a; // Eq. 10: mu = (1 - a) - a
+                sin2 = 4.0 * ua.a * ua.b;
             } else {
-                mu_new = (wd.x & 1u) ? -sqrtf(ua.u) : sqrtf(ua.u);
-                sin2 = ua.ub;
+                const double su = sqrt_newton(ua.a); // Eq. 12: mu^2 = a
+                mu_new = (wd.x & 1u) ? -su : su;
+                sin2 = ua.b;
             }
-            const float Bm = (float)Bm_;
-            const float uu = (float)Acc::val(s.U);
-            const float pp2 = 2.0f * (float)s.mub * Bm * (float)ph.inv_m;
-            float pm2 = uu * uu + pp2;
+            const double K = (double)Bm_ * P.two_over_m; // (p_perp / m)^2 = mu_B K
+            const double uu = Acc::to(s.U);
+            const double pp2 = mub_value<T>(s.mub, s.mub_lo) * K;
+            double pm2 = uu * uu + pp2, un;
             if (P.wind_u > 0.0) {
-                // the wind-frame collision of the FP64 branch above, in float
-                const float X = Acc::val(s.Rx), Y = Acc::val(s.Ry), Z = Acc::val(s.Rz);
-                const float V = (float)P.wind_u * (X * b0 + Y * b1 + Z * b2) *
-                                rsqrtf(X * X + Y * Y + Z * Z);
-                const float ic2 = (float)ph.inv_c2;
-                const float gV = rsqrtf(1.0f - V * V * ic2);
-                const float gam = sqrtf(1.0f + pm2 * ic2);
-                const float ut = gV * (uu - V * gam);
+                // the wind-frame collision of the FP64 branch above
+                const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
+                const double V = P.wind_u * (X * (double)b0 + Y * (double)b1 + Z * (double)b2) *
+                                 rsqrt_newton(X * X + Y * Y + Z * Z);
+                const double gV = rsqrt_newton(1.0 - V * V * P.inv_c2);
+                const double gam = sqrt_newton(1.0 + pm2 * P.inv_c2);
+                const double ut = gV * (uu - V * gam);
                 pm2 = ut * ut + pp2;
-                const float gt = sqrtf(1.0f + pm2 * ic2);
-                s.U = df{gV * (mu_new * sqrtf(pm2) + V * gt), 0.0f};
+                const double gt = sqrt_newton(1.0 + pm2 * P.inv_c2);
+                un = gV * (mu_new * sqrt_newton(pm2) + V * gt);
             } else {
-                s.U = df{mu_new * sqrtf(pm2), 0.0f};
+                un = mu_new * sqrt_newton(pm2);
             }
-            s.mub = (T)(sin2 * pm2 * 0.5f / (Bm * (float)ph.inv_m));
+            const double mub_new = sin2 * pm2 * rcp_newton(K);
+            s.U = Acc::from(un);
+            s.mub = (T)mub_new;
+            s.mub_lo = mub_lo_of<T>(mub_new, s.mub);
             if (P.collision_form == 0)
                 s.S = df{lambda_f_of(P, E) * neg_log_u(u31(wd.z)), 0.0f};
         }
@@ -493,10 +571,10 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
             }
         }
         if (reborn || collide) {
-            RareState<T> o{s.Rx, s.Ry, s.Rz, s.U, s.S, s.mub, s.t_birth, s.event, s.ncoll};
+            RareState<T> o{s.Rx, s.Ry, s.Rz, s.U, s.S, s.mub, s.mub_lo, s.t_birth, s.event, s.ncoll};
             o = rare_event<T>(P, ph, i, reborn, o, ax.Bm, ax.b[0], ax.b[1], ax.b[2], t0, kk);
             s.Rx = o.Rx; s.Ry = o.Ry; s.Rz = o.Rz; s.U = o.U; s.S = o.S;
-            s.mub = o.mub; s.t_birth = o.t_birth; s.event = o.event; s.ncoll = o.ncoll;
+            s.mub = o.mub; s.mub_lo = o.mub_lo; s.t_birth = o.t_birth; s.event = o.event; s.ncoll = o.ncoll;
             if (reborn)
                 ++n_reb;
             else
@@ -571,7 +649,7 @@ constexpr int kMinBlocksF32Pot = GC_PUSH_F32_POT_MIN_BLOCKS;
 constexpr int kMinBlocksF64 = GC_PUSH_F64_MIN_BLOCKS;
 
 // Fused push: one thread owns a particle for all the steps of a launch and evaluates the
-// grid field inline (one copy of the evaluation serves all phases: instruction cache).
+// grid field inline.
 template <typename T, bool TD, int POT>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : (POT == POT_ON ? kMinBlocksF32Pot : kMinBlocksF32)) : kMinBlocksF64) push_kernel(const __grid_constant__ GridMeta<T> gm, const __grid_constant__ Phys<T> ph,
                                                    const __grid_constant__ PushParams P)
@@ -591,6 +669,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
     // time-dependent fields: time of the call's start after the first snapshot
     const T tr0 = TD ? (T)(t0 - gm.t_snap0) : T(0);
     constexpr bool kRestartOutOfLine = POT != POT_ON;
+    // the two phases of a step as straight-line code (each with its own copy of the field
+    // evaluation) in the steady-field kernels; the time-dependent ones keep one copy in a
+    // loop over the phases (unrolled, they spill)
+    constexpr bool kUnrollPhases = kRestartOutOfLine && !TD;
 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.st.n; i += stride) {
         PConst c;
@@ -611,8 +693,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
             // phase 0: predictor point and corrector; phase 1: F^{n+1}, free path, events;
             // after an event, phases 2-3 restart the history: out of line, except in the
             // potential-channel variant, where that measured slower (it spills there)
-#pragma unroll 1
-            for (int phase = 0; phase < (kRestartOutOfLine ? 2 : n_phase); ++phase) {
+            auto run_phase = [&](int phase) {
                 T px, py, pz, pu;
                 phase_point(phase, s, w, dtT, px, py, pz, pu);
                 T Fo[4];
@@ -621,6 +702,15 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                                               phase == 3 ? t_end - dtT : t_end);
                 phase_consume(phase, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, t0, (long long)(P.kbase + k + 1),
                               n_coll, n_reb);
+            };
+            if constexpr (kUnrollPhases) {
+#pragma unroll
+                for (int phase = 0; phase < 2; ++phase)
+                    run_phase(phase);
+            } else {
+#pragma unroll 1
+                for (int phase = 0; phase < (kRestartOutOfLine ? 2 : n_phase); ++phase)
+                    run_phase(phase);
             }
             if (kRestartOutOfLine && n_phase == 4) {
                 using Acc = AccOf<T>;
@@ -892,6 +982,7 @@ __global__ void __launch_bounds__(128) split_kernel(const __grid_constant__ Phys
             const double mub = (1.0 - d.mu0 * d.mu0) * d.pm * d.pm * P.m / (2.0 * Bm);
             s.U = Acc::from(u);
             s.mub = (float)mub;
+            s.mub_lo = (float)(mub - (double)s.mub);
             rhs(smp, ph, Q.ideal, (float)u, (float)mub, Fo, ax);
             phase_consume(2, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
             Q.list[k] = (int32_t)i;
