@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h> // CUcontext and cuCtxGetCurrent's type only; the function comes from the runtime
 #include <cuda_runtime.h>
 
 #include "../../include/gcpush.h"
@@ -35,6 +36,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GC_NOALLOC_SCRA
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
 constexpr double kAU = 1.495978707e11;
 constexpr double kKeV = 1.602176634e-16;
@@ -54,19 +56,42 @@ int nfail(int code, const char *fmt, ...)
     return code;
 }
 
-// Device address of the scratch on `device` (which must be current). The first call per
-// device looks the symbol up; later calls reuse the cached address.
+// The current CUDA context (the device's primary context once the runtime has used it), or
+// nullptr if the driver cannot be asked; cuCtxGetCurrent is looked up through the runtime.
+CUcontext current_context()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    static const GetCurrent fn = []() -> GetCurrent {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<GetCurrent>(p);
+    }();
+    CUcontext c = nullptr;
+    return (fn && fn(&c) == CUDA_SUCCESS) ? c : nullptr;
+}
+
+// Device address of the scratch on `device` (which must be current). The first call on a
+// device looks the symbol up, and so does the first call after that device's context was
+// replaced (cudaDeviceReset), since the address belongs to the context; other calls reuse
+// the cached address.
 int scratch_address(int device, unsigned char **out)
 {
     if (device < 0 || device >= kMaxDevices)
         return nfail(GC_ERR_INVALID, "gc_advance_noalloc: device %d out of range", device);
+    const CUcontext ctx = current_context();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
+    if (!g_scratch_addr[device] || !ctx || ctx != g_scratch_ctx[device]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return nfail(GC_ERR_CUDA, "gc_advance_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         g_scratch_addr[device] = p;
+        g_scratch_ctx[device] = ctx;
     }
     *out = static_cast<unsigned char *>(g_scratch_addr[device]);
     return GC_OK;
@@ -98,7 +123,8 @@ extern "C" int gc_advance_noalloc(const gc_options *opt, const gc_grid_desc *g, 
     if (g->dtype != want_dtype)
         return nfail(GC_ERR_INVALID, "gc_advance_noalloc: grid dtype must be %s for this precision "
                      "(no conversion without scratch)", want_dtype == GC_DTYPE_F64 ? "F64" : "F32");
-    if (g->n_r < 2 || g->n_th < 2 || g->n_ph < 2 || !(g->r_min_au > 0.0) || !(g->r_max_au > g->r_min_au))
+    if (g->n_r < 2 || g->n_th < 2 || g->n_ph < 2 || !(g->r_min_au > 0.0) || !(g->r_max_au > g->r_min_au) ||
+        g->ideal < 0 || g->ideal > 2)
         return nfail(GC_ERR_INVALID, "gc_advance_noalloc: bad grid descriptor");
     if ((size_t)g->n_r * g->n_th * g->n_ph * 8 >= ((size_t)1 << 32))
         return nfail(GC_ERR_INVALID, "gc_advance_noalloc: grid exceeds the 2^32 index range");
@@ -213,12 +239,15 @@ extern "C" int gc_advance_noalloc(const gc_options *opt, const gc_grid_desc *g, 
     P.seed = opt->seed;
     P.m = mass;
     P.c2 = kC * kC;
+    P.two_over_m = 2.0 / mass;
+    P.inv_c2 = 1.0 / (kC * kC);
     P.tally_on = 0;
     P.gflags = d_flags;
     P.counters = d_counters;
 
     const int block = 128;
-    int nb = gcp::push_max_blocks_per_sm(opt->precision, block);
+    int nb = gcp::push_max_blocks_per_sm(opt->precision, block, false, g->ideal == 2);
+    cudaGetLastError(); // the occupancy query's status is not this call's
     if (nb < 1) nb = 1;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, opt->device);

@@ -9,7 +9,9 @@ and uses nothing but a fixed scratch array compiled into the library.
 Here torch tensors stand in for the caller's buffers. The entry point is called twice in
 a row through the C ABI (so the second call runs on scratch the first call left behind)
 and each result is compared with gc_advance of a context holding the same particles:
-integer state exactly, the continuous state within the FP64 parity tolerance (1e-9).
+integer state exactly, the continuous state within the FP64 parity tolerance (1e-9). A warm
+call leaves the device's free memory exactly as it found it, and the largest ensemble table
+the scratch holds (GC_NOALLOC_MAX_ENSEMBLES) gives the results of gc_advance too.
 This file is collected last and also passes on its own in a fresh process.
 """
 import ctypes as C
@@ -60,7 +62,7 @@ def _soa(dev, n):
     return s
 
 
-def _noalloc(precision, nodes_dev, dev, n, t0, step0, dt, n_steps, n_ens=None, dtype=None):
+def _noalloc(precision, nodes_dev, dev, n, t0, step0, dt, n_steps, n_ens=None, dtype=None, ens=None):
     L = gcpush.load()
     o = gcpush.Options()
     o.precision, o.device, o.seed = precision, 0, 13
@@ -70,7 +72,8 @@ def _noalloc(precision, nodes_dev, dev, n, t0, step0, dt, n_steps, n_ens=None, d
     g.dtype = dtype if dtype is not None else (gcpush.DTYPE_F64 if precision == gcpush.PREC_FP64
                                                else gcpush.DTYPE_F32)
     g.r_min_au, g.r_max_au, g.ideal = WIND.r_min_au, WIND.r_max_au, 1
-    ens = list(ENS) if n_ens is None else [ENS[0]] * n_ens
+    if ens is None:
+        ens = list(ENS) if n_ens is None else [ENS[0]] * n_ens
     arr = (gcpush.EnsembleDesc * len(ens))(*[gcpush.ensemble_desc(e) for e in ens])
     st = gcpush.StatsOut()
     rc = L.gc_advance_noalloc(C.byref(o), C.byref(g), C.c_void_p(nodes_dev.data_ptr()), arr, len(ens),
@@ -127,3 +130,51 @@ def test_noalloc_rejects_oversize_and_wrong_grid_type():
     dev["ens"][3] = 7
     rc, _ = _noalloc(gcpush.PREC_FP32_MIXED, nodes_dev, dev, n, 0.0, 0, 0.5, 5)
     assert rc == -1 and b"ensemble" in gcpush.load().gc_last_error()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After one warm call (which loads the kernels), a call leaves cudaMemGetInfo's free
+    device memory unchanged to the byte."""
+    nodes = synth.wind_grid(WIND, dtype=np.float32)
+    nodes_dev = torch.from_numpy(nodes).cuda()
+    with gcpush.Context(precision=gcpush.PREC_FP32_MIXED, seed=13) as ctx:
+        ctx.field_load(nodes, WIND.r_min_au, WIND.r_max_au)
+        ctx.inject(list(ENS))
+        dev = _to_device(ctx.get_state())
+        n = ctx.n
+    rc, _ = _noalloc(gcpush.PREC_FP32_MIXED, nodes_dev, dev, n, 0.0, 0, 0.5, 20)
+    assert rc == gcpush.GC_OK, gcpush.load().gc_last_error()
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    rc, _ = _noalloc(gcpush.PREC_FP32_MIXED, nodes_dev, dev, n, 10.0, 20, 0.5, 20)
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc == gcpush.GC_OK, gcpush.load().gc_last_error()
+    assert free1 == free0, (free0, free1, total)
+
+
+def test_noalloc_full_ensemble_table():
+    """GC_NOALLOC_MAX_ENSEMBLES (256) ensembles of two electrons each, every one with its own
+    site, energy, free path and scattering law, so that the whole table is read: the result
+    equals gc_advance's on a context injected with the same ensembles."""
+    ens = [synth.EnsembleSpec(2, r0_au=0.25 + 0.001 * k, lat_deg=-30.0 + 0.23 * k, lon_deg=1.4 * k,
+                              E0_keV=20.0 + k, lam_au=0.01 + 0.004 * k, r_out_au=R_OUT, scatter_law=k % 2)
+           for k in range(256)]
+    nodes = synth.wind_grid(WIND, dtype=np.float64)
+    nodes_dev = torch.from_numpy(nodes).cuda()
+    with gcpush.Context(precision=gcpush.PREC_FP64, seed=13, dt_init=0.5) as ctx:
+        ctx.field_load(nodes, WIND.r_min_au, WIND.r_max_au)
+        ctx.inject(ens)
+        dev = _to_device(ctx.get_state())
+        n = ctx.n
+        ctx.advance(0.5, 60)
+        ref = ctx.get_state()
+        s = ctx.stats()
+    assert int(ref["ens"].max()) == 255
+    rc, st = _noalloc(gcpush.PREC_FP64, nodes_dev, dev, n, 0.0, 0, 0.5, 60, ens=ens)
+    assert rc == gcpush.GC_OK, gcpush.load().gc_last_error()
+    got = _to_host(dev)
+    for k in gcpush.U32_STATE:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    err = compare_states(got, ref, 1e-9, momentum_scale(ref, nodes, WIND, ens))
+    assert max(err.values()) < 1e-9, err
+    assert st.collisions == s["collisions"] and st.rebirths == s["rebirths"]
