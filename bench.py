@@ -49,32 +49,54 @@ UNIT = "particle-steps/s"
 # executed count and the issue ceiling are reported beside it.
 FLOP_PER_PSTEP = 2 * (236 + 228) + 121
 FLOP_PER_PSTEP_NOMINAL = 2000
-# FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300
-# DRAM bytes (read + write) of one push launch of the default workload (3x10^6 particles,
-# 1000 steps per launch), from one ncu capture of the current kernel
-# (profiles/push_kernel_fp32_parker256_3e6.md); reported only for that launch shape
-PUSH_TRAFFIC_BYTES = 492_272_000 + 372_708_000
-# thread instructions one particle-step of the FP32 push issues (smsp__inst_executed x
-# threads per warp instruction / particle-steps, same capture): the kernel is issue-bound,
-# and 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz / this count is its issue ceiling
-PUSH_THREAD_INSTR_PER_PSTEP = 980
-PUSH_TRAFFIC_SHAPE = (3_000_000, 1000)
-# share of peak the FP64 push keeps its double-precision pipe busy (sm__pipe_fp64_cycles_active,
-# one ncu capture of the current kernel: profiles/push_kernel_fp64_parker256_300k.md); the
-# flop fraction counts a square root, reciprocal or arctangent as one flop and so reads lower
-FP64_PIPE_ACTIVE_NCU = 0.882
+# FP32 peak from the unit counts (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz), reported
+# beside the measured one (gc_fma_peak)
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_NOMINAL_TFLOPS = 1.25  # nominal dense FP64 of a GB300
+# ncu counters of the push kernels (DRAM bytes of one launch, thread instructions per
+# particle-step, FP64 pipe activity), with the sha256 of the kernel sources they were taken on
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "push_counters.txt")
+COUNTER_SOURCES = ("gc_push.cu", "gc_device.cuh", "gc_internal.h", "unit_circle_table.h")
 SM_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 # Neural field: tensor-core work of one evaluation with its Jacobian (value + 3 tangent
 # rows through three 256 x 256 layers and the 256 x 8 output layer, FMA = 2 flop)
 NEURAL_FLOP_PER_EVAL = 3 * 4 * 256 * 256 * 2 + 4 * 256 * 8 * 2
-NEURAL_STEPS_PER_CALL = 10
+# the neural path is timed over a steady window of NEURAL_TIMED_CALLS calls of
+# NEURAL_STEPS_PER_CALL push steps (10^3 steps) after one warm-up call; the large workload's
+# network push over LARGE_CALLS calls of LARGE_NEURAL_STEPS
+NEURAL_STEPS_PER_CALL = 100
+NEURAL_TIMED_CALLS = 10
+LARGE_NEURAL_STEPS = 10
 # SIREN parameters: BF16 hidden and output weights (3 x 256 x 256 + 8 x 256), FP32 first-layer
 # weights and biases (256 x 3 + 4 x 256 + 8)
 NETWORK_BYTES = 2 * (3 * 65536 + 2048) + 4 * (768 + 4 * 256 + 8)
 # timed advance calls per path on the large workload (after one warm-up call)
 LARGE_CALLS = 2
+
+
+def push_counters() -> dict:
+    """The ncu counters of the push kernels, or {"stale": True, ...} without them when the
+    kernel sources have changed since they were taken."""
+    import hashlib
+
+    vals, h = {}, hashlib.sha256()
+    for name in COUNTER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_06706_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    try:
+        for line in open(COUNTERS_FILE):
+            parts = line.split("#", 1)[0].split()
+            if len(parts) == 2:
+                vals[parts[0]] = parts[1]
+    except OSError:
+        return {"stale": True, "reason": "no counters file"}
+    if vals.get("kernel_sources_sha256") != h.hexdigest():
+        return {"stale": True, "reason": "kernel sources changed since the ncu capture"}
+    out = {"stale": False}
+    for k, v in vals.items():
+        if k != "kernel_sources_sha256":
+            out[k] = float(v)
+    return out
 
 
 def workload(n_per_lambda: int = 1_000_000):
@@ -243,11 +265,14 @@ def run_reference(args, rank, world):
     value = st.n * ref_steps * args.steps / el
     sample = (f"{st.n} particles (first 512 ids of each lambda ensemble) x {ref_steps} steps per "
               f"bench step, FP64 oracle, {cores} host threads")
+    config = config_dict(wl, sum(e.count for e in wl.ensembles))
+    config["timed_sample"] = {"particles": st.n, "push_steps_per_step": ref_steps,
+                              "ids": "the first 512 of each lambda ensemble"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(wl, sum(e.count for e in wl.ensembles)),
+        "data": "synthetic", "config": config,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -333,10 +358,9 @@ def neural_bench(args, nodes, local, stream, rank):
     # push with the network as the field source
     c.field_select(gcpush.FIELD_SIREN)
     c.inject(list(wn.ensembles))
-    for _ in range(args.warmup):
-        c.advance(wn.dt, NEURAL_STEPS_PER_CALL)
+    c.advance(wn.dt, NEURAL_STEPS_PER_CALL)
     s0 = c.stats()
-    ms = _timed_calls(c, stream, wn.dt, NEURAL_STEPS_PER_CALL, args.steps)
+    ms = _timed_calls(c, stream, wn.dt, NEURAL_STEPS_PER_CALL, NEURAL_TIMED_CALLS)
     s1 = c.stats()
     n = wn.n_particles
     evals = s1["field_evals"] - s0["field_evals"]
@@ -346,8 +370,10 @@ def neural_bench(args, nodes, local, stream, rank):
     peak = peaks.get("bf16_tflops_sustained")
     c.close()
     return {
-        "workload": wn.name, "particles": n, "value": n * NEURAL_STEPS_PER_CALL * args.steps / (ms / 1e3),
-        "unit": UNIT, "ms_per_step": ms / (args.steps * NEURAL_STEPS_PER_CALL),
+        "workload": wn.name, "particles": n,
+        "value": n * NEURAL_STEPS_PER_CALL * NEURAL_TIMED_CALLS / (ms / 1e3),
+        "unit": UNIT, "ms_per_step": ms / (NEURAL_TIMED_CALLS * NEURAL_STEPS_PER_CALL),
+        "push_steps": NEURAL_TIMED_CALLS * NEURAL_STEPS_PER_CALL, "warmup_push_steps": NEURAL_STEPS_PER_CALL,
         "roofline": {"bound": "tensor", "kernel": "siren_eval_kernel", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
                      "peak_basis": "measured bf16 cuBLAS, sustained (MEASURED_PEAKS.json)",
@@ -406,13 +432,13 @@ def large_bench(args, local, stream, rank):
     err = _siren_error(c, w)
     c.field_select(gcpush.FIELD_SIREN)
     c.inject(list(wl.ensembles))
-    c.tally_arm(**dict(tally, cadence=NEURAL_STEPS_PER_CALL))
-    c.advance(wl.dt, NEURAL_STEPS_PER_CALL)
-    ms = _timed_calls(c, stream, wl.dt, NEURAL_STEPS_PER_CALL, LARGE_CALLS)
+    c.tally_arm(**dict(tally, cadence=LARGE_NEURAL_STEPS))
+    c.advance(wl.dt, LARGE_NEURAL_STEPS)
+    ms = _timed_calls(c, stream, wl.dt, LARGE_NEURAL_STEPS, LARGE_CALLS)
     t = c.tally_read()
-    out["neural"] = {"value": n * NEURAL_STEPS_PER_CALL * LARGE_CALLS / (ms / 1e3), "unit": UNIT,
-                     "push_steps": NEURAL_STEPS_PER_CALL * LARGE_CALLS,
-                     "warmup_push_steps": NEURAL_STEPS_PER_CALL,
+    out["neural"] = {"value": n * LARGE_NEURAL_STEPS * LARGE_CALLS / (ms / 1e3), "unit": UNIT,
+                     "push_steps": LARGE_NEURAL_STEPS * LARGE_CALLS,
+                     "warmup_push_steps": LARGE_NEURAL_STEPS,
                      "tally_samples": int(t["n_seen"][0]), "tally_out_of_range": int(t["n_seen"][1]),
                      "training": _training_dict(X, X["schedule"], loss, t_fit),
                      "field_rel_rms_vs_grid": err}
@@ -553,6 +579,8 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     gcpush.build()
+    fp32_peak, fp64_peak = gcpush.fma_peak(local)
+    counters = push_counters()
     wl = workload(args.particles // 3)
     n_rank = wl.n_particles
     nodes = synth.wind_grid(wl.wind, dtype=np.float32)
@@ -597,21 +625,29 @@ def main():
     pstep_rate = n_rank * steps_per_launch / (push_ms / 1e3)  # particle-steps/s of one launch
     achieved = FLOP_PER_PSTEP_NOMINAL * pstep_rate / 1e12
     executed = FLOP_PER_PSTEP * pstep_rate / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": (PUSH_TRAFFIC_BYTES if (n_rank, round(steps_per_launch)) == PUSH_TRAFFIC_SHAPE
-                            else None),
+    fresh = not counters["stale"]
+    same_shape = fresh and (n_rank, round(steps_per_launch)) == (counters.get("push_fp32.launch_particles"),
+                                                                   counters.get("push_fp32.launch_steps"))
+    instr = counters.get("push_fp32.thread_instr_per_particle_step") if fresh else None
+    issue_ceiling = 152 * 4 * 32 * 2.07e9 / instr if instr else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": int(counters["push_fp32.dram_bytes_per_launch"]) if same_shape else None,
                 "kernel": "push_kernel<float>", "launch_ms": push_ms,
                 "flop_per_particle_step": FLOP_PER_PSTEP_NOMINAL,
                 "flop_basis": "the method's algorithmic work per particle-step (two field evaluations "
                               "with 8-corner value and gradient weights of 8 channels and full "
                               "Jacobians, the right-hand side, predictor and corrector)",
                 "executed": {"flop_per_particle_step": FLOP_PER_PSTEP, "achieved": executed,
-                             "frac": executed / FP32_PEAK_TFLOPS},
-                "issue": {"thread_instr_per_particle_step": PUSH_THREAD_INSTR_PER_PSTEP,
-                          "ceiling_particle_steps_per_s": 152 * 4 * 32 * 2.07e9 / PUSH_THREAD_INSTR_PER_PSTEP,
-                          "frac": pstep_rate / (152 * 4 * 32 * 2.07e9 / PUSH_THREAD_INSTR_PER_PSTEP)},
-                "peak_basis": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)",
+                             "frac": executed / fp32_peak},
+                "issue": {"thread_instr_per_particle_step": instr, "ceiling_particle_steps_per_s": issue_ceiling,
+                          "frac": pstep_rate / issue_ceiling if issue_ceiling else None},
+                "peak_basis": "measured: gc_fma_peak (independent FP32 FMA chains on every SM, best of 5 "
+                              "launches, CUDA events), taken just before the timed region",
+                "peak_derived": FP32_PEAK_DERIVED_TFLOPS,
+                "frac_of_derived": achieved / FP32_PEAK_DERIVED_TFLOPS,
+                "counters": "profiles/push_counters.txt" + (" (stale: sources changed since the ncu capture; "
+                                                             "traffic and issue left null)" if not fresh else ""),
                 "push_share_of_step": (s1["push_ms"] - s0["push_ms"]) / el_ms}
     gpu_launches = s1["kernel_launches"] - s0["kernel_launches"]
     clocks = clk.summary()
@@ -665,12 +701,13 @@ def main():
         a64 = FLOP_PER_PSTEP * v64 / world / 1e12
         fp64 = {"value": v64, "unit": UNIT, "push_steps": n64,
                 "note": "same workload, FP64 grid and arithmetic; timed after the same start-up",
-                "roofline": {"bound": "fp64", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": a64 / FP64_PEAK_TFLOPS, "flop_per_particle_step": FLOP_PER_PSTEP,
+                "roofline": {"bound": "fp64", "achieved": a64, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": a64 / fp64_peak, "flop_per_particle_step": FLOP_PER_PSTEP,
                              "flop_basis": "executed (the nominal 2.0 kflop would exceed the FP64 peak: "
                                            "this kernel runs the regrouped right-hand side too)",
-                             "peak_basis": "nominal GB300 FP64 rate (no measured figure)",
-                             "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE_NCU}}
+                             "peak_basis": "measured: gc_fma_peak (independent FP64 FMA chains on every SM)",
+                             "peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
+                             "fp64_pipe_active_ncu": counters.get("push_fp64.fp64_pipe_active") if fresh else None}}
         c64.close()
 
     # ---------------- 64 uneven ensembles, graph replay, autotuned launch shape -------------

@@ -203,8 +203,11 @@ int gc_particles_inject(gc_ctx *ctx, const gc_ensemble_desc *e, int n_ens);
  * Synchronises the stream; GC_ERR_DEVICE_ANOMALY if any particle was flagged. */
 int gc_advance(gc_ctx *ctx, double dt, int64_t n_steps, double lambda_au);
 
-/* Tallies. If out != NULL the current counts are copied to the host first; then, if
- * arm != NULL, the tallies are (re)armed with that descriptor and zeroed. */
+/* Snapshot tallies (Sect. 3: every `cadence` steps, the particles (re)born at or after
+ * t_start_s are binned by pitch cosine, kinetic energy and r; by age and energy inside the
+ * [rwin_lo, rwin_hi) window at 1 AU; young pitch distributions; sin^2 alpha per r bin). If
+ * out != NULL the current counts are copied to the host first; then, if arm != NULL, the
+ * tallies are (re)armed with that descriptor and zeroed. */
 int gc_tally(gc_ctx *ctx, const gc_tally_desc *arm, gc_tally_out *out);
 
 /* Copy the particle state to / from host arrays (in id order of the last set/inject;
@@ -257,6 +260,15 @@ int gc_sort(gc_ctx *ctx);
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int gc_version(void);
+
+/* Measured fused multiply-add throughput of GPU `device`, in TFLOP/s (an FMA counts as two
+ * flops): *fp32_tflops for float, *fp64_tflops for double. These are the peaks the push
+ * kernels are measured against (no counterpart in the paper). Each rate is the best of five
+ * launches of about 10 ms of independent FMA chains on every SM, timed with CUDA events on a
+ * stream of its own, which is created, synchronised and destroyed inside the call; the
+ * current device is restored. GC_ERR_INVALID for a missing device or a null pointer,
+ * GC_ERR_CUDA if a launch fails. */
+int gc_fma_peak(int device, double *fp32_tflops, double *fp64_tflops);
 
 /* BF16 tensor-core GEMM used by the neural-field training: C = A B^T with A (M x K) and
  * B (N x K) bf16 row-major on the device (K contiguous, 16-byte aligned), FP32 accumulate,
@@ -363,8 +375,8 @@ int gc_field_select(gc_ctx *ctx, int source);
  * pool and hands out views of its buffers, or a stepping loop that must not pay the
  * device-wide synchronisation an allocation can cause.
  *
- * It runs the push kernel of gc_advance (Eqs. 1-6, scattering, rebirth; no tallies and
- * no cell sort) on:
+ * It runs the push kernel of gc_advance (with scattering and rebirth; no tallies and no
+ * cell sort) on:
  *   opt       precision, device, stream, seed and the physics switches (dt_init and
  *             id_base are not used);
  *   g, grid_dev   the field grid already on the device, in the precision's type (F64 for
@@ -377,8 +389,9 @@ int gc_field_select(gc_ctx *ctx, int source);
  *             lambda_au as for gc_advance;
  *   stats_out optional: collisions, rebirths and flags of this call.
  * The ensemble table, the anomaly flag and the event counters live in one file-scope
- * device array of GC_NOALLOC_SCRATCH_BYTES. The first call on a device looks up that
- * array's device address; make that first call before any stream capture on the device.
+ * device array of GC_NOALLOC_SCRATCH_BYTES. The first call on a device (and the first after
+ * its context was reset) looks up that array's device address; make that first call before
+ * any stream capture on the device.
  * Every call overwrites the array (the status words are cleared at the start of each
  * call), so calls whose work overlaps on the GPU race on it: serialise them. Returns
  * GC_ERR_INVALID for more ensembles than the maximum, a wrong grid type or an ens id out

@@ -20,7 +20,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libgcpush.so")
 SOURCES = ("gc_api.cu", "gc_push.cu", "gc_sort.cu", "gc_noalloc.cu", "gc_siren.cu", "gc_siren_eval.cu",
-           "gc_neural.cu")
+           "gc_neural.cu", "gc_peak.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
@@ -156,7 +156,7 @@ EXPORTS = ("gc_create", "gc_destroy", "gc_last_error", "gc_field_load", "gc_part
            "gc_set_launch", "gc_sort", "gc_version", "gc_set_clock", "gc_advance_noalloc",
            "gc_set_graph", "gc_autotune", "gc_gemm_bf16_tn", "gc_gemm_bf16", "gc_siren_set", "gc_siren_get",
            "gc_siren_eval", "gc_siren_field", "gc_field_targets", "gc_siren_loss_grad", "gc_field_fit",
-           "gc_field_select", "gc_field_load_next")
+           "gc_field_select", "gc_field_load_next", "gc_fma_peak")
 
 _lib = None
 
@@ -201,6 +201,7 @@ def load(path: str | None = None):
         "gc_sort": (C.c_int, [vp]),
         "gc_version": (C.c_int, []),
         "gc_set_clock": (C.c_int, [vp, C.c_double, C.c_int64]),
+        "gc_fma_peak": (C.c_int, [C.c_int, _DP, _DP]),
         "gc_advance_noalloc": (C.c_int, [C.POINTER(Options), C.POINTER(GridDesc), vp,
                                          C.POINTER(EnsembleDesc), C.c_int, C.POINTER(ParticleSoA),
                                          C.c_double, C.c_int64, C.c_double, C.c_int64, C.c_double,
@@ -212,6 +213,13 @@ def load(path: str | None = None):
         fn.argtypes = args
     _lib = L
     return L
+
+
+def fma_peak(device: int = 0) -> tuple[float, float]:
+    """Measured FP32 and FP64 FMA throughput of the device (TFLOP/s), gc_fma_peak."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().gc_fma_peak(int(device), C.byref(a), C.byref(b)), "gc_fma_peak")
+    return a.value, b.value
 
 
 class GcError(RuntimeError):
