@@ -433,16 +433,19 @@ __device__ __forceinline__ void gather(const GridMeta<T> &gm, T x, T y, T z, Sam
     if (xr < T(-1) || xr > T(gm.n_r))
         flags |= FLAG_OUT_OF_GRID;
 
-    int i = (int)m_floor(xr);
-    T fr = xr - T(i);
+    const T flr = m_floor(xr);
+    int i = (int)flr;
+    T fr = xr - flr;
     if (i < 0) { i = 0; fr = T(0); }
     else if (i > gm.n_r - 2) { i = gm.n_r - 2; fr = T(1); }
-    int j = (int)m_floor(xt);
-    T ft = xt - T(j);
+    const T flt = m_floor(xt);
+    int j = (int)flt;
+    T ft = xt - flt;
     if (j < 0) { j = 0; ft = T(0); }
     else if (j > gm.n_th - 2) { j = gm.n_th - 2; ft = T(1); }
-    int k = (int)m_floor(xp);
-    const T fp = xp - T(k);
+    const T flp = m_floor(xp);
+    int k = (int)flp;
+    const T fp = xp - flp;
     if (k >= gm.n_ph) k -= gm.n_ph;
     if (k < 0) k += gm.n_ph;
     const int k1 = (k + 1 == gm.n_ph) ? 0 : k + 1;

@@ -13,8 +13,6 @@
 // field and Eqs. 1-2 in float and accumulates R, gamma v_par and the free path in
 // double-float pairs; mu_B is a double-float too (the right-hand side takes its float
 // part), and the rare collision and rebirth updates of gamma v_par and mu_B run in double.
-#include <type_traits>
-
 #include "gc_device.cuh"
 #include "gc_internal.h"
 
@@ -200,27 +198,25 @@ __device__ __noinline__ void tally_sample(const TallyDev &T_, const PushParams &
 }
 
 // ----------------------------------------------------------------------------------------
-// mu_B of the FP32 path is a double-float: the float the right-hand side takes and a low
-// part for the collision bookkeeping; the FP64 path has no low part.
-struct NoLo {
-};
-template <typename T>
-using MubLo = typename std::conditional<sizeof(T) == 4, float, NoLo>::type;
+// mu_B of the FP32 path is a double-float: the float the right-hand side takes (in the
+// particle state) and a low part that only the collision bookkeeping and the launch's load
+// and store touch, kept in a per-thread shared-memory slot instead of a register the step
+// loop would carry. Blocks of the push kernels have at most kMaxPushBlock threads.
+constexpr int kMaxPushBlock = 128;
+__shared__ float s_mub_lo[kMaxPushBlock];
 
 template <typename T>
-__device__ __forceinline__ MubLo<T> mub_lo_of(double d, T hi)
+__device__ __forceinline__ void mub_lo_set(double d, T hi)
 {
     if constexpr (sizeof(T) == 4)
-        return (float)(d - (double)hi);
-    else
-        return NoLo{};
+        s_mub_lo[threadIdx.x] = (float)(d - (double)hi);
 }
 
 template <typename T>
-__device__ __forceinline__ double mub_value(T hi, MubLo<T> lo)
+__device__ __forceinline__ double mub_value(T hi)
 {
     if constexpr (sizeof(T) == 4)
-        return (double)hi + (double)lo;
+        return (double)hi + (double)s_mub_lo[threadIdx.x];
     else
         return (double)hi;
 }
@@ -237,9 +233,7 @@ template <typename T>
 struct PState {
     using A = typename AccOf<T>::A;
     A Rx, Ry, Rz, U, S;
-    T mub;
-    MubLo<T> mub_lo;
-    T F0[4], F1[4], vpar0, hprev, Bm0;
+    T mub, F0[4], F1[4], vpar0, hprev, Bm0;
     double t_birth;
     uint32_t event, ncoll, flags;
 };
@@ -247,7 +241,7 @@ struct PState {
 // constants of one particle that the step loop reads every step; the rest of its ensemble's
 // constants are read from the table where an event needs them
 struct PConst {
-    float ri2, ro2;
+    float ri2, ro2; // squared shell radii moved 1e-5 inward: beyond them a rebirth is decided in double
     uint32_t e;
 };
 
@@ -272,15 +266,15 @@ __device__ __forceinline__ void load_particle(const PushParams &P, int64_t i, PC
     using Acc = AccOf<T>;
     const int64_t cap = P.st.cap;
     c.e = P.st.ens[i];
-    c.ri2 = P.ens[c.e].r_in2;
-    c.ro2 = P.ens[c.e].r_out2;
+    c.ri2 = P.ens[c.e].r_in2 * (1.0f + 1e-5f);
+    c.ro2 = P.ens[c.e].r_out2 * (1.0f - 1e-5f);
     s.Rx = Acc::from(P.st.x[i]);
     s.Ry = Acc::from(P.st.y[i]);
     s.Rz = Acc::from(P.st.z[i]);
     s.U = Acc::from(P.st.u[i]);
     s.S = Acc::from(P.st.s_rem[i]);
     s.mub = (T)P.st.mub[i];
-    s.mub_lo = mub_lo_of<T>(P.st.mub[i], s.mub);
+    mub_lo_set<T>(P.st.mub[i], s.mub);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         s.F0[k] = (T)P.st.F0[k * cap + i];
@@ -305,7 +299,7 @@ __device__ __forceinline__ void store_particle(const PushParams &P, int64_t i, c
     P.st.z[i] = Acc::to(s.Rz);
     P.st.u[i] = Acc::to(s.U);
     P.st.s_rem[i] = Acc::to(s.S);
-    P.st.mub[i] = mub_value<T>(s.mub, s.mub_lo);
+    P.st.mub[i] = mub_value<T>(s.mub);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         P.st.F0[k * cap + i] = (double)s.F0[k];
@@ -407,7 +401,6 @@ template <typename T>
 struct RareState {
     typename AccOf<T>::A Rx, Ry, Rz, U, S;
     T mub;
-    MubLo<T> mub_lo;
     double t_birth;
     uint32_t event, ncoll;
 };
@@ -440,7 +433,7 @@ __device__ __noinline__ RareState<T> rare_event(const PushParams &P, const Phys<
         }
         s.U = Acc::from(P.st.u_inj[i]);
         s.mub = (T)P.st.mub_inj[i];
-        s.mub_lo = mub_lo_of<T>(P.st.mub_inj[i], s.mub);
+        mub_lo_set<T>(P.st.mub_inj[i], s.mub);
         s.ncoll = 0;
         s.t_birth = step_time(t0, kk, P.dt);
     } else {
@@ -492,7 +485,7 @@ __device__ __noinline__ RareState<T> rare_event(const PushParams &P, const Phys<
             }
             const double K = (double)Bm_ * P.two_over_m; // (p_perp / m)^2 = mu_B K
             const double uu = Acc::to(s.U);
-            const double pp2 = mub_value<T>(s.mub, s.mub_lo) * K;
+            const double pp2 = mub_value<T>(s.mub) * K;
             double pm2 = uu * uu + pp2, un;
             if (P.wind_u > 0.0) {
                 // the wind-frame collision of the FP64 branch above
@@ -511,7 +504,7 @@ __device__ __noinline__ RareState<T> rare_event(const PushParams &P, const Phys<
             const double mub_new = sin2 * pm2 * rcp_newton(K);
             s.U = Acc::from(un);
             s.mub = (T)mub_new;
-            s.mub_lo = mub_lo_of<T>(mub_new, s.mub);
+            mub_lo_set<T>(mub_new, s.mub);
             if (P.collision_form == 0)
                 s.S = df{lambda_f_of(P, E) * neg_log_u(u31(wd.z)), 0.0f};
         }
@@ -560,21 +553,19 @@ __device__ __forceinline__ void phase_consume(int phase, int &n_phase, int64_t i
             } else {
                 const float xx = (float)px, yy = (float)py, zz = (float)pz;
                 const float r2 = xx * xx + yy * yy + zz * zz;
-                if (fabsf(r2 - c.ri2) < 1e-5f * c.ri2 || fabsf(r2 - c.ro2) < 1e-5f * c.ro2) {
-                    // near the shell: decide in double from the accumulated position
+                if (r2 < c.ri2 || r2 > c.ro2) {
+                    // near or beyond the shell: decide in double from the accumulated position
                     const double X = Acc::to(s.Rx), Y = Acc::to(s.Ry), Z = Acc::to(s.Rz);
                     const double r1 = sqrt(X * X + Y * Y + Z * Z);
                     reborn = (r1 < P.ens[c.e].r_in || r1 > P.ens[c.e].r_out);
-                } else {
-                    reborn = (r2 < c.ri2 || r2 > c.ro2);
                 }
             }
         }
         if (reborn || collide) {
-            RareState<T> o{s.Rx, s.Ry, s.Rz, s.U, s.S, s.mub, s.mub_lo, s.t_birth, s.event, s.ncoll};
+            RareState<T> o{s.Rx, s.Ry, s.Rz, s.U, s.S, s.mub, s.t_birth, s.event, s.ncoll};
             o = rare_event<T>(P, ph, i, reborn, o, ax.Bm, ax.b[0], ax.b[1], ax.b[2], t0, kk);
             s.Rx = o.Rx; s.Ry = o.Ry; s.Rz = o.Rz; s.U = o.U; s.S = o.S;
-            s.mub = o.mub; s.mub_lo = o.mub_lo; s.t_birth = o.t_birth; s.event = o.event; s.ncoll = o.ncoll;
+            s.mub = o.mub; s.t_birth = o.t_birth; s.event = o.event; s.ncoll = o.ncoll;
             if (reborn)
                 ++n_reb;
             else
@@ -726,8 +717,6 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                 s.flags |= o.flags;
             }
             s.hprev = dtT;
-            if (!(m_finite(AccOf<T>::val(s.Rx)) && m_finite(AccOf<T>::val(s.U)) && m_finite(s.F0[0])))
-                s.flags |= FLAG_NONFINITE;
 
             if (k == next_tally) {
                 next_tally += P.tally.cadence;
@@ -737,6 +726,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                                 s.t_birth >= P.tally.t_start && (int)c.e < P.tally.n_ens);
             }
         }
+        // a non-finite position is flagged by the gather at the next evaluation; what the last
+        // step leaves is checked here
+        if (!(m_finite(AccOf<T>::val(s.Rx)) && m_finite(AccOf<T>::val(s.U)) && m_finite(s.F0[0])))
+            s.flags |= FLAG_NONFINITE;
         store_particle(P, i, s);
     }
     // counters: one atomic per warp
@@ -982,7 +975,7 @@ __global__ void __launch_bounds__(128) split_kernel(const __grid_constant__ Phys
             const double mub = (1.0 - d.mu0 * d.mu0) * d.pm * d.pm * P.m / (2.0 * Bm);
             s.U = Acc::from(u);
             s.mub = (float)mub;
-            s.mub_lo = (float)(mub - (double)s.mub);
+            mub_lo_set<float>(mub, s.mub);
             rhs(smp, ph, Q.ideal, (float)u, (float)mub, Fo, ax);
             phase_consume(2, n_phase, i, s, c, Fo, ax, w, P, ph, dtT, P.t0, Q.kk, n_coll, n_reb);
             Q.list[k] = (int32_t)i;
@@ -1093,6 +1086,8 @@ InjectFn<T> inject_fn(bool td, bool pot)
 cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, const PushParams &p,
                         int block, int grid, cudaStream_t s)
 {
+    if (block < 1 || block > kMaxPushBlock)
+        return cudaErrorInvalidConfiguration;
     cudaGetLastError(); // report this launch only
     const bool td = g.nodes1 != nullptr, pot = g.ideal == 2;
     if (precision == 0)
