@@ -96,29 +96,43 @@ def momentum_scale(st, nodes, wind, ens) -> np.ndarray:
     return np.sqrt(st["u_inj"] ** 2 + 2 * st["mub_inj"] * b / M_E)
 
 
-def compare_states(g, o, tol, pm, skip=None, lam=None):
-    """Max relative errors of the continuous state; pm: per-particle |p|/m scale; lam:
-    per-particle mean free path (the scale of the remaining free path; 0.01 AU if None)."""
-    keep = np.ones(g["x"].shape[0], dtype=bool) if skip is None else ~skip
+def state_errors(g, o, pm, keep=None, lam=None):
+    """Per-particle relative errors of the continuous state (arrays over the kept particles);
+    pm: per-particle |p|/m scale; lam: per-particle mean free path (the scale of the remaining
+    free path; 0.01 AU if None)."""
+    keep = np.ones(g["x"].shape[0], dtype=bool) if keep is None else keep
     R = np.stack([g["x"], g["y"], g["z"]])[:, keep]
     Ro = np.stack([o["x"], o["y"], o["z"]])[:, keep]
     out = {}
-    out["R"] = np.max(np.linalg.norm(R - Ro, axis=0) / np.linalg.norm(Ro, axis=0))
-    out["u"] = np.max(np.abs(g["u"][keep] - o["u"][keep]) / pm[keep])
-    out["vpar"] = np.max(np.abs(g["vpar"][keep] - o["vpar"][keep]) / pm[keep])
+    out["R"] = np.linalg.norm(R - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
+    out["u"] = np.abs(g["u"][keep] - o["u"][keep]) / pm[keep]
+    out["vpar"] = np.abs(g["vpar"][keep] - o["vpar"][keep]) / pm[keep]
     mscale = np.maximum(np.abs(o["mub"][keep]), 1e-30 + np.abs(o["mub_inj"][keep]).max() * 1e-6)
-    out["mub"] = np.max(np.abs(g["mub"][keep] - o["mub"][keep]) / mscale)
+    out["mub"] = np.abs(g["mub"][keep] - o["mub"][keep]) / mscale
     for F in ("F0", "F1"):
         # dR/dt = v_par b + drifts: near a mirror point v_par -> 0 and |dR/dt| shrinks to the
         # drift speed while its error still follows the v_par error, which scales with |p|/m;
         # so the scale is |dR/dt| but not below a tenth of |p|/m
         v = np.maximum(np.linalg.norm(o[F][:3, keep], axis=0), 0.1 * pm[keep])
-        out[F + "_R"] = np.max(np.linalg.norm(g[F][:3, keep] - o[F][:3, keep], axis=0) / v)
+        out[F + "_R"] = np.linalg.norm(g[F][:3, keep] - o[F][:3, keep], axis=0) / v
         # d(gamma v_par)/dt: the mirror force is ~ v^2 / L ~ (|p|/m) / 1000 s
-        out[F + "_u"] = np.max(np.abs(g[F][3, keep] - o[F][3, keep]) / (pm[keep] / 1000.0))
+        out[F + "_u"] = np.abs(g[F][3, keep] - o[F][3, keep]) / (pm[keep] / 1000.0)
     ls = (0.01 * AU) if lam is None else lam[keep]
-    out["s_rem"] = np.max(np.abs(g["s_rem"][keep] - o["s_rem"][keep]) / ls)
+    out["s_rem"] = np.abs(g["s_rem"][keep] - o["s_rem"][keep]) / ls
     return out
+
+
+def compare_states(g, o, tol, pm, skip=None, lam=None):
+    """Max relative errors of the continuous state (state_errors) over the particles not in
+    skip."""
+    keep = np.ones(g["x"].shape[0], dtype=bool) if skip is None else ~skip
+    return {k: float(np.max(v)) if v.size else 0.0 for k, v in state_errors(g, o, pm, keep, lam).items()}
+
+
+def bulk_percentiles(g, o, pm, skip=None, lam=None, q=99):
+    """The q-th percentile of every relative state error over the particles not in skip."""
+    keep = np.ones(g["x"].shape[0], dtype=bool) if skip is None else ~skip
+    return {k: float(np.percentile(v, q)) for k, v in state_errors(g, o, pm, keep, lam).items()}
 
 
 def ill_conditioned(nodes, wind, ens, calls, final, pm, eps=3e-7, n_dir=2, **kw):
