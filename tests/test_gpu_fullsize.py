@@ -5,7 +5,7 @@ particles one by one: the first 512 ids of every ensemble (Philox streams are ke
 particle id, so a subset evolves exactly as inside the full ensemble).
 
 Tolerances: the trajectory state (R, gamma v_par, v_par, mu_B, free path) within 1e-4 over
-the first 10^3 steps, and its bulk (99th percentile of the position error) within 1e-5.
+the first 10^3 steps, and its bulk (99th percentile of every state error) within 2e-5.
 The carried right-hand sides F^n, F^{n-1} are functions of the state; in a field with
 10 % structure on 0.1 AU scales a position offset dR moves b and grad|B| by about
 0.1 dR / 0.1 AU, so they are held to 1e-3. The tail of the FP32 errors comes from the rare
@@ -15,12 +15,33 @@ import numpy as np
 import pytest
 
 import oracle
-from _cases import compare_states, momentum_scale, oracle_ensembles
+from _cases import bulk_percentiles, compare_states, momentum_scale, oracle_ensembles
 from oracle import AU
 from paper_2403_06706_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 gcpush = pytest.importorskip("paper_2403_06706_gb300.gcpush")
+
+# The bulk of the kept particles must sit far inside the per-particle maxima (1e-4, 1e-3 for
+# the carried right-hand sides), so that an error confined to more than 1 % of the
+# trajectories cannot hide below the maxima or behind the particles excused for a differing
+# history or an ill-conditioned start: the 99th percentile of every state error within
+# 2e-5, ten times the FP32 rounding a state accumulates over 10^3 steps (sqrt(1000) x 6e-8
+# ~ 2e-6), and of the carried right-hand sides within 1e-4 (their maxima's tenfold ratio to
+# the state's). Measured: p99 of 2e-7 to 5e-6 for the state, up to 1.2e-5 for F^n, F^{n-1};
+# medians near 1e-7.
+BULK_P99 = {"R": 2e-5, "u": 2e-5, "vpar": 2e-5, "mub": 2e-5, "s_rem": 2e-5, "F0_R": 1e-4, "F0_u": 1e-4,
+            "F1_R": 1e-4, "F1_u": 1e-4}
+
+
+def _check_bulk(name, gs, st, pm, skip, lam):
+    p50 = bulk_percentiles(gs, st, pm, skip=skip, lam=lam, q=50)
+    p99 = bulk_percentiles(gs, st, pm, skip=skip, lam=lam, q=99)
+    print(name, "excused", int(skip.sum()), "of", skip.size)
+    for k in p99:
+        print(f"  {k:6s} p50 {p50[k]:.2e}  p99 {p99[k]:.2e}")
+    for k, v in p99.items():
+        assert v < BULK_P99[k], (name, k, v)
 
 
 def test_full_size_fp32_sampled_parity():
@@ -55,10 +76,11 @@ def test_full_size_fp32_sampled_parity():
     div = (gs["ncoll"] != st["ncoll"]) | (gs["event"] != st["event"]) | (gs["t_birth"] != st["t_birth"])
     assert div.mean() <= 0.01, div.sum()
     lam = np.array([e.lam_au for e in wl.ensembles])[st["ens"].astype(int)] * AU
-    err = compare_states(gs, st.arrays, 1e-4, momentum_scale(st, nodes, wl.wind, wl.ensembles),
-                         skip=div, lam=lam)
+    pm = momentum_scale(st, nodes, wl.wind, wl.ensembles)
+    err = compare_states(gs, st.arrays, 1e-4, pm, skip=div, lam=lam)
     for k, v in err.items():
         assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+    _check_bulk("plain", gs, st.arrays, pm, div, lam)
     keep = ~div
     R = np.stack([gs["x"], gs["y"], gs["z"]])[:, keep]
     Ro = np.stack([st["x"], st["y"], st["z"]])[:, keep]
@@ -112,10 +134,11 @@ def test_large_grid_fp32_sampled_parity_and_tally_invariants():
     div = (gs["ncoll"] != st["ncoll"]) | (gs["event"] != st["event"]) | (gs["t_birth"] != st["t_birth"])
     assert div.mean() <= 0.02, div.sum()
     lam = np.full(n_s, wl.ensembles[0].lam_au * AU)
-    err = compare_states(gs, st.arrays, 1e-4, momentum_scale(st, nodes, wl.wind, wl.ensembles),
-                         skip=div, lam=lam)
+    pm = momentum_scale(st, nodes, wl.wind, wl.ensembles)
+    err = compare_states(gs, st.arrays, 1e-4, pm, skip=div, lam=lam)
     for k, v in err.items():
         assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+    _check_bulk("large", gs, st.arrays, pm, div, lam)
 
 
 def test_neural_workload_sampled_parity():
@@ -279,6 +302,7 @@ def test_full_size_variants_sampled_parity(variant):
     err = compare_states(gs, st.arrays, 1e-4, pm, skip=div, lam=lam)
     for k, v in err.items():
         assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+    _check_bulk(variant, gs, st.arrays, pm, div, lam)
     keep = ~div
     R = np.stack([gs["x"], gs["y"], gs["z"]])[:, keep]
     Ro = np.stack([st["x"], st["y"], st["z"]])[:, keep]
