@@ -19,10 +19,14 @@ namespace gcp {
 
 enum : uint32_t { FLAG_OUT_OF_GRID = 1u, FLAG_AXIS = 2u, FLAG_NONFINITE = 4u };
 
-// Whether an evaluation uses the potential channel (two-fluid E_par, Sect. 2.2): decided at
-// compile time for the fused push (the grid's mode is known at launch), at run time from
-// GridMeta::ideal == 2 for the split-step kernels.
-enum : int { POT_NONE = 0, POT_ON = 1, POT_RUNTIME = -1 };
+// How an evaluation takes E_par: decided at compile time for the fused push (the grid's mode
+// is known at launch), at run time from GridMeta::ideal for the split-step kernels.
+//   POT_IDEAL  ideal mode (ideal == 1): E_par = 0, its terms compiled out
+//   POT_NONE   no potential channel, E_par from the run-time mode (E.b or 0)
+//   POT_ON     the two-fluid potential channel (ideal == 2): E_par = -b.grad(Phi)
+// The fused push gathers from the grid, whose phi-index gradient has no z component; the
+// split-step kernels (POT_RUNTIME) may take Cartesian derivatives from other sources.
+enum : int { POT_NONE = 0, POT_ON = 1, POT_IDEAL = 2, POT_RUNTIME = -1 };
 
 // ----------------------------------------------------------------------------------------
 // Philox-4x32-10: ten rounds of two 32x32 -> 64 multiplies; the two key words are bumped
@@ -591,10 +595,13 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 #pragma unroll
     for (int d = 0; d < 3; ++d)
         sb[d] = s.dB[d][0] * b[0] + s.dB[d][1] * b[1] + s.dB[d][2] * b[2];
+    // the grid's phi-index gradient has no z component (g[2][2] = 0)
+    constexpr bool kGridG = POT != POT_RUNTIME;
     T gB[3];
 #pragma unroll
     for (int jx = 0; jx < 3; ++jx)
-        gB[jx] = sb[0] * s.g[0][jx] + sb[1] * s.g[1][jx] + sb[2] * s.g[2][jx];
+        gB[jx] = (kGridG && jx == 2) ? sb[0] * s.g[0][2] + sb[1] * s.g[1][2]
+                                     : sb[0] * s.g[0][jx] + sb[1] * s.g[1][jx] + sb[2] * s.g[2][jx];
     const T b_gB = dot3(b, gB);
 
     // E x B drift
@@ -606,8 +613,9 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 
     // ideal 1: E_par = 0 (ideal Ohm's law); 0: the interpolated E.b; 2: the two-fluid
     // correction -grad(Phi) (Sect. 2.2): E_par = -b.grad(Phi) = -sum_d dPhi/di_d (g_d . b)
-    T Epar;
-    if (POT == POT_ON || (POT == POT_RUNTIME && ideal == 2)) {
+    T Epar = T(0);
+    if constexpr (POT == POT_IDEAL) {
+    } else if (POT == POT_ON || (POT == POT_RUNTIME && ideal == 2)) {
         T pb[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d)
@@ -626,7 +634,10 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             F[c] = vpar * b[c];
-        F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB;
+        if constexpr (POT == POT_IDEAL)
+            F[3] = -(mub * ph.inv_m * inv_g * b_gB);
+        else
+            F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB;
     } else {
         // Every directional derivative of Eqs. 1-2 is along w = v_par b + v_E (the guiding
         // centre's velocity without the drifts): the bracket's v_par^2 (b.grad)b +
@@ -639,7 +650,7 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
         T pw[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-            pw[d] = dot3(s.g[d], wv);
+            pw[d] = (kGridG && d == 2) ? s.g[2][0] * wv[0] + s.g[2][1] * wv[1] : dot3(s.g[d], wv);
         T JBw[3], JEw[3];
         jvec2(s.dB, s.dE, pw, JBw, JEw);
         const T w_gB = dot3(wv, gB);
@@ -658,11 +669,17 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 
         // Eq. 1 bracket
         const T c_gB = mub * ph.inv_m * inv_g * inv_g;
-        const T c_vE = ph.qm * vpar * Epar * ph.inv_c2 * inv_g;
         T br[3];
+        if constexpr (POT == POT_IDEAL) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            br[c] = c_gB * gB[c] + c_vE * vE[c] + vpar * wgb[c] + wgv[c];
+            for (int c = 0; c < 3; ++c)
+                br[c] = c_gB * gB[c] + vpar * wgb[c] + wgv[c];
+        } else {
+            const T c_vE = ph.qm * vpar * Epar * ph.inv_c2 * inv_g;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                br[c] = c_gB * gB[c] + c_vE * vE[c] + vpar * wgb[c] + wgv[c];
+        }
         // time-dependent fields: v_par db/dt + dv_E/dt in the bracket, and db/dt in Eq. 2's
         // v_E product, with db/dt = (dB/dt - b (b.dB/dt)) / B and
         // dv_E/dt = (dE/dt x B + E x dB/dt) / B^2 - 2 v_E (b.dB/dt) / B
@@ -689,7 +706,10 @@ __device__ __forceinline__ void rhs(const Sample<T> &s, const Phys<T> &ph, int i
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             w2[c] = wgb[c] + dbdt[c];
-        F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB + gamma * dot3(vE, w2);
+        if constexpr (POT == POT_IDEAL)
+            F[3] = gamma * dot3(vE, w2) - mub * ph.inv_m * inv_g * b_gB;
+        else
+            F[3] = ph.qm * Epar - mub * ph.inv_m * inv_g * b_gB + gamma * dot3(vE, w2);
     }
     aux.gamma = gamma;
     aux.vpar = vpar;

@@ -659,11 +659,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                          dtT * T(-1.0 / 12.0)};
     // time-dependent fields: time of the call's start after the first snapshot
     const T tr0 = TD ? (T)(t0 - gm.t_snap0) : T(0);
-    constexpr bool kRestartOutOfLine = POT != POT_ON;
     // the two phases of a step as straight-line code (each with its own copy of the field
     // evaluation) in the steady-field kernels; the time-dependent ones keep one copy in a
     // loop over the phases (unrolled, they spill)
-    constexpr bool kUnrollPhases = kRestartOutOfLine && !TD;
+    constexpr bool kUnrollPhases = !TD;
 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.st.n; i += stride) {
         PConst c;
@@ -682,8 +681,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
             const T t_end = TD ? tr0 + (T)(P.kbase + k + 1) * dtT : T(0);
             int n_phase = 2;
             // phase 0: predictor point and corrector; phase 1: F^{n+1}, free path, events;
-            // after an event, phases 2-3 restart the history: out of line, except in the
-            // potential-channel variant, where that measured slower (it spills there)
+            // after an event, phases 2-3 restart the history out of line
             auto run_phase = [&](int phase) {
                 T px, py, pz, pu;
                 phase_point(phase, s, w, dtT, px, py, pz, pu);
@@ -700,10 +698,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (TD ? kMinBlocksF32TD : 
                     run_phase(phase);
             } else {
 #pragma unroll 1
-                for (int phase = 0; phase < (kRestartOutOfLine ? 2 : n_phase); ++phase)
+                for (int phase = 0; phase < 2; ++phase)
                     run_phase(phase);
             }
-            if (kRestartOutOfLine && n_phase == 4) {
+            if (n_phase == 4) {
                 using Acc = AccOf<T>;
                 const Restart<T> o = restart_history<T, TD, POT>(gm, ph, Acc::val(s.Rx), Acc::val(s.Ry),
                                                                  Acc::val(s.Rz), Acc::val(s.U), s.mub, dtT, t_end);
@@ -1067,12 +1065,13 @@ using PushFn = void (*)(const GridMeta<T>, const Phys<T>, const PushParams);
 template <typename T>
 using InjectFn = void (*)(const GridMeta<T>, const Phys<T>, const InjectParams);
 
+// ideal: the grid's mode is 1 (E_par = 0), which has a variant of its own
 template <typename T>
-PushFn<T> push_fn(bool td, bool pot)
+PushFn<T> push_fn(bool td, bool pot, bool ideal)
 {
     if (td)
-        return pot ? push_kernel<T, true, POT_ON> : push_kernel<T, true, POT_NONE>;
-    return pot ? push_kernel<T, false, POT_ON> : push_kernel<T, false, POT_NONE>;
+        return pot ? push_kernel<T, true, POT_ON> : (ideal ? push_kernel<T, true, POT_IDEAL> : push_kernel<T, true, POT_NONE>);
+    return pot ? push_kernel<T, false, POT_ON> : (ideal ? push_kernel<T, false, POT_IDEAL> : push_kernel<T, false, POT_NONE>);
 }
 
 template <typename T>
@@ -1089,11 +1088,11 @@ cudaError_t launch_push(int precision, const GridHost &g, const PhysHost &ph, co
     if (block < 1 || block > kMaxPushBlock)
         return cudaErrorInvalidConfiguration;
     cudaGetLastError(); // report this launch only
-    const bool td = g.nodes1 != nullptr, pot = g.ideal == 2;
+    const bool td = g.nodes1 != nullptr, pot = g.ideal == 2, ideal = g.ideal == 1;
     if (precision == 0)
-        push_fn<double>(td, pot)<<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
+        push_fn<double>(td, pot, ideal)<<<grid, block, 0, s>>>(make_meta<double>(g), make_phys<double>(ph), p);
     else
-        push_fn<float>(td, pot)<<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
+        push_fn<float>(td, pot, ideal)<<<grid, block, 0, s>>>(make_meta<float>(g), make_phys<float>(ph), p);
     return cudaGetLastError();
 }
 
@@ -1151,9 +1150,9 @@ cudaError_t preload_kernels()
 {
     cudaFuncAttributes a;
     cudaError_t e = cudaSuccess;
-    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
-        e = cudaFuncGetAttributes(&a, push_fn<float>(v & 1, v & 2));
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_fn<double>(v & 1, v & 2));
+    for (int v = 0; v < 8 && e == cudaSuccess; ++v) {
+        e = cudaFuncGetAttributes(&a, push_fn<float>(v & 1, v & 2, v & 4));
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, push_fn<double>(v & 1, v & 2, v & 4));
     }
     return e;
 }
@@ -1162,9 +1161,9 @@ int push_max_blocks_per_sm(int precision, int block, bool time_dependent, bool p
 {
     int nb = 0;
     if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_fn<double>(time_dependent, potential), block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_fn<double>(time_dependent, potential, !potential), block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_fn<float>(time_dependent, potential), block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, push_fn<float>(time_dependent, potential, !potential), block, 0);
     return nb;
 }
 

@@ -7,12 +7,15 @@ library's own kernels on the 64x32x64 Parker grid.
    evaluations of the network differ by rounding flips of the BF16 values carried between
    layers (tests/test_gpu_siren.py holds them to 1e-3 RMS / 2e-2 max of the outputs' RMS for
    values and 2e-3 / 3e-2 for the Jacobian). Along a trajectory that noise enters every
-   step: a field direction off by e moves the position increment by e |dR| and the mirror
-   force by e_J of its size. Even if the noise kept one sign over the whole path, the increments
-   of R would stay within e |Delta R| and those of gamma v_par within e_J |Delta u| + (the
-   mirror force's share). The test holds the particles with the same collision and rebirth
-   history as the oracle (>= 95 % of them) to those bounds with e = 1e-3, e_J = 2e-3 (RMS)
-   and the maxima at 2e-2, 3e-2.
+   step: a field direction off by e moves the position by e per unit of path travelled and
+   the mirror force by e_J of its size. Even if the noise kept one sign over the whole path,
+   the position would stay within e L (L: the path travelled since the particle's last
+   (re)birth, |v| times the time; for the diffusive particles of the short mean free path
+   it is far longer than their net displacement) and gamma v_par within e_J of |p|/m. The
+   test holds the particles with the same collision and rebirth history as the oracle
+   (>= 95 % of them) to those bounds with e = 1e-3, e_J = 2e-3 (RMS) and the maxima at 2e-2,
+   3e-2. (The training accumulates its gradients with floating-point atomics, so each run
+   trains a slightly different network; the bounds hold for any of them.)
 2. What the trained network gains over the grid it was trained on, on the path users run:
    the same electrons with E = 0 and no scattering, pushed by gc_advance in FP32 through the
    grid and through the network at dt = 2, 1 and 0.5 s for 240 s. With E = 0 gamma is
@@ -88,12 +91,11 @@ def test_neural_push_matches_oracle_over_1000_steps(trained):
     print("same history", same.mean(), "collisions", int(o["ncoll"].sum()),
           "rebirths", int((o["t_birth"] > 0).sum()))
     assert same.mean() >= 0.95 and int(o["ncoll"].sum()) > 100
-    # increments from the particle's last (re)birth state: the injection state, or for a
-    # reborn particle its site and injection momentum
     R = lambda s: np.stack([s["x"], s["y"], s["z"]])  # noqa: E731
     pm = np.sqrt(o0["u"] ** 2 + 2 * o0["mub"] * _absB(f, o0) / M_E)  # |p|/m at injection
-    dRo = R(o) - R(o0)  # reborn particles restart at the injection site
-    eR = np.linalg.norm(R(g1) - R(o), axis=0) / np.maximum(np.linalg.norm(dRo, axis=0), 1e-3 * AU)
+    speed = pm / np.sqrt(1.0 + (pm / C_LIGHT) ** 2)  # |v|, kept by the inertial-frame collisions
+    path = speed * (n_steps * 0.5 - o["t_birth"])     # travelled since the last (re)birth
+    eR = np.linalg.norm(R(g1) - R(o), axis=0) / path
     eu = np.abs(g1["u"] - o["u"]) / pm
     emu = np.abs(g1["mub"] - o["mub"]) / np.maximum(np.abs(o["mub"]), 1e-3 * np.abs(o0["mub"]).max())
     for name, e in (("R", eR), ("u", eu), ("mu_B", emu)):
@@ -163,7 +165,9 @@ def test_network_gain_through_the_library(trained):
     assert order_g < 1.5 and egy_g[0.5][1] < 0.6 * egy_g[2.0][1]
     # the network on the BF16 tensor-core path: a floor set by the evaluation noise of its
     # Jacobian (which drives the mirror force), the same at every dt within a factor 2,
-    # whether gamma is taken with the library's |B| or with the exact network's
+    # whether gamma is taken with the library's |B| or with the exact network's; its level
+    # (3e-5 to 1e-4 in the median over the networks the non-deterministic training gives)
+    # within 5e-4
     for e in (egy_s, egy_x):
         med = [e[dt][1] for dt in (2.0, 1.0, 0.5)]
-        assert max(med) < 2.0 * min(med) and max(med) < 1e-4
+        assert max(med) < 2.0 * min(med) and max(med) < 5e-4
