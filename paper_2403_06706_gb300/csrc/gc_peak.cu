@@ -11,11 +11,21 @@
 namespace {
 
 constexpr int kChains = 8;
+
+// written only if a chain's sum equals -1, which these inputs never give; the test keeps
+// every chain live without a store per thread
+__device__ float g_fma_sink_f;
+__device__ double g_fma_sink_d;
+
+template <typename T> __device__ __forceinline__ T *fma_sink();
+template <> __device__ __forceinline__ float *fma_sink<float>() { return &g_fma_sink_f; }
+template <> __device__ __forceinline__ double *fma_sink<double>() { return &g_fma_sink_d; }
+
 constexpr int kBlock = 256;
 constexpr int kBlocksPerSM = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) fma_rate_kernel(T *out, int iters, T a, T b)
+__global__ void __launch_bounds__(kBlock) fma_rate_kernel(int iters, T a, T b)
 {
     T x[kChains];
 #pragma unroll
@@ -30,8 +40,8 @@ __global__ void __launch_bounds__(kBlock) fma_rate_kernel(T *out, int iters, T a
 #pragma unroll
     for (int c = 0; c < kChains; ++c)
         s += x[c];
-    if (s == (T)-1) // never true for these inputs; keeps every chain live
-        out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (s == (T)-1)
+        *fma_sink<T>() = s;
 }
 
 template <typename T>
@@ -49,7 +59,7 @@ int rate(int sms, int iters, cudaStream_t st, double *tflops)
     int rc = GC_OK;
     for (int k = 0; k < 6 && rc == GC_OK; ++k) { // launch 0 warms up
         cudaEventRecord(e0, st);
-        fma_rate_kernel<T><<<blocks, kBlock, 0, st>>>(nullptr, iters, a, b);
+        fma_rate_kernel<T><<<blocks, kBlock, 0, st>>>(iters, a, b);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = GC_ERR_CUDA;
