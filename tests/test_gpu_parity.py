@@ -340,6 +340,36 @@ def test_two_fluid_field_matches_oracle(precision):
     assert np.abs(g["u"] - gi["u"]).max() > 1e-7 * pm.max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_non_ideal_field_matches_oracle(precision):
+    """A field with a parallel electric component taken from the interpolated E (ideal mode
+    0: E_par = E.b, the bracket's E_par v_E term and Eq. 2's q E_par of Eqs. 1-2): the Parker
+    grid with E + k B (k = 2 m/s, E_par ~ 1e-8 V/m, a few keV over an AU), against the oracle;
+    the parallel force must change the trajectories relative to the ideal field."""
+    dtype = np.float64 if precision == "fp64" else np.float32
+    prec = gcpush.PREC_FP64 if precision == "fp64" else gcpush.PREC_FP32_MIXED
+    nodes = synth.wind_grid(WIND, dtype=np.float64)
+    nodes[..., 3:6] += 2.0 * nodes[..., 0:3]
+    nodes = nodes.astype(dtype)
+    calls = [(0.5, 300, 0.0)]
+    g, _, gs = run_gpu(nodes, WIND, ENS, calls, prec, seed=29, ideal=False)
+    o, _, os_ = run_oracle(nodes, WIND, ENS, calls, seed=29, ideal=False)
+    pm = momentum_scale(o, nodes, WIND, ENS)
+    if precision == "fp64":
+        _ints_equal(g, o)
+        err = compare_states(g, o.arrays, 1e-9, pm)
+        for k, v in err.items():
+            assert v < 1e-9, (k, v, err)
+    else:
+        div = (g["ncoll"] != o["ncoll"]) | (g["event"] != o["event"]) | (g["t_birth"] != o["t_birth"])
+        assert div.mean() <= 0.02
+        err = compare_states(g, o.arrays, 1e-4, pm, skip=div)
+        for k, v in err.items():
+            assert v < (1e-3 if k.startswith("F") else 1e-4), (k, v, err)
+    gi, _, _ = run_gpu(nodes, WIND, ENS, calls, prec, seed=29, ideal=True)
+    assert np.abs(g["u"] - gi["u"]).max() > 1e-6 * pm.max()
+
+
 WIND1 = synth.WindSpec(64, 32, 64, B1=4.2e-9, u_sw=5.0e5, eps=0.15, n_modes=4, seed=3)
 
 
