@@ -642,7 +642,7 @@ def main():
                              "frac": executed / fp32_peak},
                 "issue": {"thread_instr_per_particle_step": instr, "ceiling_particle_steps_per_s": issue_ceiling,
                           "frac": pstep_rate / issue_ceiling if issue_ceiling else None},
-                "peak_basis": "measured: gc_fma_peak (independent FP32 FMA chains on every SM, best of 5 "
+                "peak_basis": "measured: gc_fma_peak (independent FP32 FMA chains on every SM, best of 10 "
                               "launches, CUDA events), taken just before the timed region",
                 "peak_derived": FP32_PEAK_DERIVED_TFLOPS,
                 "frac_of_derived": achieved / FP32_PEAK_DERIVED_TFLOPS,

@@ -263,7 +263,7 @@ int gc_version(void);
 
 /* Measured fused multiply-add throughput of GPU `device`, in TFLOP/s (an FMA counts as two
  * flops): *fp32_tflops for float, *fp64_tflops for double. These are the peaks the push
- * kernels are measured against (no counterpart in the paper). Each rate is the best of five
+ * kernels are measured against (no counterpart in the paper). Each rate is the best of ten
  * launches of about 10 ms of independent FMA chains on every SM, timed with CUDA events on a
  * stream of its own, which is created, synchronised and destroyed inside the call; the
  * current device is restored. GC_ERR_INVALID for a missing device or a null pointer,
