@@ -60,8 +60,14 @@ __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
 }
 
 // ----------------------------------------------------------------------------------------
-// Double-float accumulator (hi + lo, |lo| <= ulp(hi)/2): Knuth's TwoSum followed by a
-// fast renormalisation. Used by the FP32 path for R, gamma v_par and the free path.
+// Double-float accumulator (hi + lo, |lo| <= ulp(hi)/2), used by the FP32 path for R,
+// gamma v_par and the free path. Adding a float b: the increment joins the low word first,
+// l = lo + b (the one rounding, 2^-24 relative to l, i.e. to the increment whenever the
+// increment exceeds ulp(hi)), then Dekker's Fast2Sum moves l into the high word:
+// h = hi + l, lo' = l - (h - hi), and h + lo' = hi + l exactly whenever |hi| >= |l|. That
+// fails only while the accumulated value is as small as its increments (a component of R
+// or gamma v_par passing through zero, the free path's last step), where the error is a
+// rounding of that small value.
 struct df {
     float hi, lo;
 };
@@ -76,12 +82,9 @@ __device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.
 
 __device__ __forceinline__ df df_add(df a, float b)
 {
-    const float s = __fadd_rn(a.hi, b);
-    const float bb = __fsub_rn(s, a.hi);
-    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    e = __fadd_rn(e, a.lo);
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+    const float l = __fadd_rn(a.lo, b);
+    const float h = __fadd_rn(a.hi, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, a.hi))};
 }
 
 // ----------------------------------------------------------------------------------------
