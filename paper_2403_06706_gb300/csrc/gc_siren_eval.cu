@@ -16,10 +16,13 @@
 // N = 16 with W5 zero-padded). Weights stream through a 6-stage TMA ring (16 KB chunks of
 // 64 input features x 128 outputs); the first layer runs on the CUDA cores.
 //
-// Pipeline of one layer: the MMAs of output half 0 (all K), then half 1 in two K halves.
-// The epilogue of half 0 overlaps the MMAs of half 1 (it may overwrite input features
-// 0-127 once half 1 has consumed them), and the epilogue of half 1 overlaps the next
-// layer's half-0 MMAs over input features 0-127 (the features half 0 has just written).
+// Pipeline of one layer, in MMA order: half 0 over input features 0-127, half 1 over 0-127,
+// half 0 over 128-255, half 1 over 128-255. The epilogue of half 0 (features 0-127) starts
+// when half 0 is complete, and with it every MMA of the layer over inputs 0-127, so it may
+// overwrite them at once; it overlaps the MMAs of half 1 over 128-255. The epilogue of half
+// 1 says when it has read its whole accumulator (h1_drained, halfway through): the next
+// layer's MMAs over inputs 0-127 (the features half 0 has just written), half 0's during it
+// and half 1's after that signal, run while it computes; those over 128-255 follow it.
 // The output layer also runs in two K halves (input features 0-127 during the last
 // epilogue of half 1, then 128-255) into columns 0-31 of the drained half-0 accumulator,
 // and overlaps the next tile's first layer: its half 0 is written once the output MMAs over
@@ -188,8 +191,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *empty = full + kStagesW;
     uint64_t *h_ready = empty + kStagesW; // [2]: activations of a half written, its accumulator drained
     uint64_t *acc = h_ready + 2;          // [2]: accumulator of a half complete
-    uint64_t *kdone = acc + 2;            // half 1 has consumed input features 0-127
-    uint64_t *acc_out = kdone + 1;        // output layer complete
+    uint64_t *h1_drained = acc + 2;       // the half-1 epilogue has read its accumulator
+    uint64_t *acc_out = h1_drained + 1;   // output layer complete
     uint64_t *out_a = acc_out + 1;        // output-layer MMAs over input features 0-127 complete
     uint64_t *fin = out_a + 1;
     uint32_t *tmem_slot = (uint32_t *)(fin + 1);
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&h_ready[1], kComputeThreads);
         mbar_init(&acc[0], 1);
         mbar_init(&acc[1], 1);
-        mbar_init(kdone, 1);
+        mbar_init(h1_drained, kComputeThreads);
         mbar_init(acc_out, 1);
         mbar_init(out_a, 1);
         mbar_init(fin, 1);
@@ -242,9 +245,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     uint8_t *dst = sW + s * kChunkBytes;
                     if (c < 24) {
-                        // chunk (layer c / 8, output half (c / 4) % 2, input block c % 4)
+                        // chunk (layer c / 8, output half and input block in the MMA order)
+                        const int q = c & 7, h = (q >> 1) & 1, kb = (q & 1) | ((q >> 2) << 1);
                         mbar_expect_tx(&full[s], kChunkBytes);
-                        tma_load_2d(dst, &mwh, (c & 3) * 64, (c >> 3) * 256 + ((c >> 2) & 1) * 128, &full[s]);
+                        tma_load_2d(dst, &mwh, kb * 64, (c >> 3) * 256 + h * 128, &full[s]);
                     } else {
                         mbar_expect_tx(&full[s], kW5Bytes);
                         for (int kb = 0; kb < 4; ++kb)
@@ -263,39 +267,49 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id_hid = idesc_bf16_f32(128, 256, 0, 1);
             const uint32_t id_out = idesc_bf16_f32(128, 16, 1, 0);
             const uint32_t hb = smem_u32(sH);
-            uint32_t g = 0, nh0 = 0, nh1 = 0;
+            uint32_t g = 0, nh0 = 0, nh1 = 0, nd = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 for (int L = 0; L < 3 && ok; ++L) {
-                    for (int h = 0; h < 2 && ok; ++h) {
-                        for (int kb = 0; kb < 4; ++kb) {
-                            if (h == 0 && kb == 0) {
-                                // inputs 0-127 written and accumulator half 0 drained
-                                if (!wait_abort(&h_ready[0], nh0 & 1u, abort, p.err, 12)) { ok = false; break; }
-                                ++nh0;
-                                tc_fence_after();
-                            }
-                            if (h == 0 && kb == 2) {
-                                // inputs 128-255 written and accumulator half 1 drained
-                                if (!wait_abort(&h_ready[1], nh1 & 1u, abort, p.err, 13)) { ok = false; break; }
-                                ++nh1;
-                                tc_fence_after();
-                            }
-                            const uint32_t s = g % kStagesW;
-                            if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 14)) { ok = false; break; }
+                    // order: half 0 over inputs 0-127, half 1 over inputs 0-127 (as soon as the
+                    // previous half-1 epilogue has read its accumulator), half 0 over 128-255
+                    // (once that epilogue has written them), half 1 over 128-255
+#pragma unroll 1
+                    for (int q = 0; q < 8; ++q) {
+                        const int h = (q >> 1) & 1, kb = (q & 1) | ((q >> 2) << 1);
+                        if (q == 0) {
+                            // inputs 0-127 written and accumulator half 0 drained
+                            if (!wait_abort(&h_ready[0], nh0 & 1u, abort, p.err, 12)) { ok = false; break; }
+                            ++nh0;
                             tc_fence_after();
-                            const uint32_t wb = smem_u32(sW + s * kChunkBytes);
-#pragma unroll
-                            for (int ks = 0; ks < 4; ++ks)
-                                mma_bf16(tmem + h * 256, desc_sw128(wb + ks * 32),
-                                         desc_sw128_mn(hb + (kb * 4 + ks) * 8192, 1024, 4096), id_hid,
-                                         (kb | ks) ? 1u : 0u);
-                            mma_commit(&empty[s]);
-                            ++g;
-                            if (h == 1 && kb == 1) mma_commit(kdone);
                         }
-                        if (ok) mma_commit(&acc[h]);
+                        if (q == 2 && (L > 0 || t != blockIdx.x)) {
+                            // accumulator half 1 read by the previous half-1 epilogue
+                            if (!wait_abort(h1_drained, nd & 1u, abort, p.err, 19)) { ok = false; break; }
+                            ++nd;
+                            tc_fence_after();
+                        }
+                        if (q == 4) {
+                            // inputs 128-255 written
+                            if (!wait_abort(&h_ready[1], nh1 & 1u, abort, p.err, 13)) { ok = false; break; }
+                            ++nh1;
+                            tc_fence_after();
+                        }
+                        const uint32_t s = g % kStagesW;
+                        if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 14)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t wb = smem_u32(sW + s * kChunkBytes);
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks)
+                            mma_bf16(tmem + h * 256, desc_sw128(wb + ks * 32),
+                                     desc_sw128_mn(hb + (kb * 4 + ks) * 8192, 1024, 4096), id_hid,
+                                     (kb | ks) ? 1u : 0u);
+                        mma_commit(&empty[s]);
+                        ++g;
+                        // half 0 complete, and with it every MMA of this layer over inputs 0-127
+                        if (q == 5) mma_commit(&acc[0]);
                     }
+                    if (ok) mma_commit(&acc[1]);
                 }
                 if (!ok) break;
                 // output layer: rows x W5^T, M-tile 0 into columns 0-15 and M-tile 1 into 16-31
@@ -361,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t *hrow1 = hrow0 + 16 * 4096;
         const uint32_t rsw = (uint32_t)(lane & 7);
         const unsigned full_mask = 0xffffffffu;
-        uint32_t na0 = 0, na1 = 0, nk = 0, no = 0, noa = 0;
+        uint32_t na0 = 0, na1 = 0, no = 0, noa = 0;
         bool ok = true, first = true;
         int64_t base_prev = 0;
         // this warp's 16 points: lane i < 16 holds point 16 rg + i, shared by shuffles; the
@@ -451,10 +465,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     uint8_t *hrow = h ? hrow1 : hrow0;
                     const float b = bl[L][h];
+                    // (half 0: every MMA over inputs 0-127 is complete with its accumulator)
 #pragma unroll 1
                     for (int c = 0; c < 2; ++c) {
                         float v[32];
                         tmem_ld32(lane_base + h * 256 + rg * 64 + c * 32, v);
+                        if (h == 1 && c == 1) {
+                            // the half-1 accumulator is read: the next layer's half-1 MMAs
+                            // over inputs 0-127 may run during the rest of this epilogue
+                            tc_fence_before();
+                            mbar_arrive(h1_drained);
+                        }
                         float o[4][8];
 #pragma unroll
                         for (int pp = 0; pp < 4; ++pp)
@@ -470,19 +491,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 o[pp][4 * e + 2] = cs * v[q0 + 2];
                                 o[pp][4 * e + 3] = cs * v[q0 + 3];
                             }
-                        if (h == 0 && c == 0) {
-                            // half 1 reads input features 0-127 until kdone
-                            if (!wait_abort(kdone, nk & 1u, abort, p.err, 19)) {
-                                ok = false;
-                                break;
-                            }
-                            ++nk;
-                        }
 #pragma unroll
                         for (int pp = 0; pp < 4; ++pp)
                             store_rows8(hrow, rsw, (uint32_t)(rg * 64 + c * 32 + 8 * pp), o[pp]);
                     }
-                    if (!ok) break;
                     fence_proxy_async_smem();
                     tc_fence_before();
                     mbar_arrive(&h_ready[h]);
