@@ -13,8 +13,9 @@
 // of the value row once and scales its own three tangent columns, with no data exchange.
 // Activations go back to shared memory in the MN-major 128-byte-swizzled layout that the
 // next layer reads as its B operand. The output layer runs as rows x W5^T (M = 128 rows,
-// N = 16 with W5 zero-padded). Weights stream through a 6-stage TMA ring (16 KB chunks of
-// 64 input features x 128 outputs); the first layer runs on the CUDA cores.
+// N = 16 with W5 zero-padded, loaded once per launch). The hidden layers' weights stream
+// through a 4-stage TMA ring (16 KB chunks of 64 input features x 128 outputs; 4 stages
+// measured faster than 5 or 6, 2 slower); the first layer runs on the CUDA cores.
 //
 // Pipeline of one layer, in MMA order: half 0 over input features 0-127, half 1 over 0-127,
 // half 0 over 128-255, half 1 over 128-255. The epilogue of half 0 (features 0-127) starts
@@ -52,15 +53,15 @@ using namespace tc;
 namespace {
 
 constexpr int kPts = 64;                        // points per tile
-constexpr int kStagesW = 6;                     // weight ring depth
+constexpr int kStagesW = 4;                     // weight ring depth
 constexpr uint32_t kChunkBytes = 128u * 128u;   // 128 output rows x 64 bf16
 constexpr uint32_t kW5Bytes = 4u * 16u * 128u;  // W5 padded: 4 boxes of 16 rows x 64 bf16
 constexpr uint32_t kHBytes = 32u * 4u * 1024u;  // 32 K-groups x 4 MN-blocks of 1024 B
-constexpr int kChunksPerTile = 3 * 8 + 1;
+constexpr int kChunksPerTile = 3 * 8;
 constexpr int kComputeThreads = 512;            // arrivals on each h_ready barrier
 constexpr int kThreads = 576;
 constexpr int kMmaWarp = 16, kTmaWarp = 17;
-constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + 1024 + 256;
+constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + kW5Bytes + 1024 + 256;
 
 struct EvalParams {
     const float *P;  // master parameters
@@ -187,7 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sH = smem;
     uint8_t *sW = smem + kHBytes;
-    uint64_t *full = (uint64_t *)(sW + kStagesW * kChunkBytes);
+    uint8_t *sW5 = sW + kStagesW * kChunkBytes;  // W5, resident for the whole launch
+    uint64_t *full = (uint64_t *)(sW5 + kW5Bytes);
     uint64_t *empty = full + kStagesW;
     uint64_t *h_ready = empty + kStagesW; // [2]: activations of a half written, its accumulator drained
     uint64_t *acc = h_ready + 2;          // [2]: accumulator of a half complete
@@ -195,7 +197,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *acc_out = h1_drained + 1;   // output layer complete
     uint64_t *out_a = acc_out + 1;        // output-layer MMAs over input features 0-127 complete
     uint64_t *fin = out_a + 1;
-    uint32_t *tmem_slot = (uint32_t *)(fin + 1);
+    uint64_t *w5full = fin + 1;           // W5 landed
+    uint32_t *tmem_slot = (uint32_t *)(w5full + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(acc_out, 1);
         mbar_init(out_a, 1);
         mbar_init(fin, 1);
+        mbar_init(w5full, 1);
         *abort = 0;
         mbar_fence_init();
     }
@@ -236,6 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             uint32_t g = 0;
             bool ok = true;
+            mbar_expect_tx(w5full, kW5Bytes);
+            for (int kb = 0; kb < 4; ++kb)
+                tma_load_2d(sW5 + kb * 2048, &mw5, kb * 64, 0, w5full);
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 for (int c = 0; c < kChunksPerTile; ++c) {
                     const uint32_t s = g % kStagesW;
@@ -244,22 +251,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t *dst = sW + s * kChunkBytes;
-                    if (c < 24) {
-                        // chunk (layer c / 8, output half and input block in the MMA order)
-                        const int q = c & 7, h = (q >> 1) & 1, kb = (q & 1) | ((q >> 2) << 1);
-                        mbar_expect_tx(&full[s], kChunkBytes);
-                        tma_load_2d(dst, &mwh, kb * 64, (c >> 3) * 256 + h * 128, &full[s]);
-                    } else {
-                        mbar_expect_tx(&full[s], kW5Bytes);
-                        for (int kb = 0; kb < 4; ++kb)
-                            tma_load_2d(dst + kb * 2048, &mw5, kb * 64, 0, &full[s]);
-                    }
+                    // chunk (layer c / 8, output half and input block in the MMA order)
+                    const int q = c & 7, h = (q >> 1) & 1, kb = (q & 1) | ((q >> 2) << 1);
+                    mbar_expect_tx(&full[s], kChunkBytes);
+                    tma_load_2d(dst, &mwh, kb * 64, (c >> 3) * 256 + h * 128, &full[s]);
                     ++g;
                 }
             }
             // the copies still in flight land before the CTA's shared memory is released
             for (uint32_t j = g > (uint32_t)kStagesW ? g - kStagesW : 0u; j < g; ++j)
                 mbar_wait(&full[j % kStagesW], (j / kStagesW) & 1u);
+            mbar_wait(w5full, 0);
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
@@ -315,18 +317,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // output layer: rows x W5^T, M-tile 0 into columns 0-15 and M-tile 1 into 16-31
                 // (both in the drained half-0 accumulator), in two K halves: input features
                 // 0-127 as soon as their epilogue is done, 128-255 after the last one
-                const uint32_t s = g % kStagesW;
                 bool ok2 = true;
+                if (t == blockIdx.x) {
+                    // W5, loaded once per launch
+                    if (!wait_abort(w5full, 0, abort, p.err, 17)) break;
+                    tc_fence_after();
+                }
                 for (int kh = 0; kh < 2 && ok2; ++kh) {
                     uint32_t &nh = kh ? nh1 : nh0;
                     if (!wait_abort(&h_ready[kh], nh & 1u, abort, p.err, 15 + kh)) { ok2 = false; break; }
                     ++nh;
                     tc_fence_after();
-                    if (kh == 0) {
-                        if (!wait_abort(&full[s], (g / kStagesW) & 1u, abort, p.err, 17)) { ok2 = false; break; }
-                        tc_fence_after();
-                    }
-                    const uint32_t wb = smem_u32(sW + s * kChunkBytes);
+                    const uint32_t wb = smem_u32(sW5);
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -338,8 +340,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (kh == 0) mma_commit(out_a);
                 }
                 if (!ok2) break;
-                mma_commit(&empty[s]);
-                ++g;
                 mma_commit(acc_out);
             }
             // all MMAs of this CTA complete before its tensor memory is released
