@@ -71,17 +71,6 @@ struct EvalParams {
     int *err;        // error word (device), set when a wait runs out
 };
 
-// sin and cos after a Cody-Waite reduction by 2 pi (2 pi split into a float and its
-// remainder), so that the hardware approximations see |r| <= pi
-__device__ __forceinline__ void sincos_rr(float z, float &s, float &c)
-{
-    const float k = rintf(z * 0.159154943091895336f);
-    float r = fmaf(-k, 6.28318548202514648f, z);
-    r = fmaf(-k, -1.74845553e-7f, r);
-    s = __sinf(r);
-    c = __cosf(r);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -416,8 +405,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float x0 = __shfl_sync(full_mask, px, src), x1 = __shfl_sync(full_mask, py, src),
                                     x2 = __shfl_sync(full_mask, pz, src);
                         const float z = w0 * fmaf(w1[h][0], x0, fmaf(w1[h][1], x1, fmaf(w1[h][2], x2, b1[h])));
-                        float sn, cs;
-                        sincos_rr(z, sn, cs);
+                        // the hardware sine and cosine on z directly (|z| reaches tens here, w0
+                        // = 30): their error, a few 1e-6 at most there, stays three orders below
+                        // the BF16 rounding of the activations; an explicit reduction by 2 pi
+                        // first cost 2 % of the kernel for no gain against the exact network
+                        const float sn = __sinf(z), cs = __cosf(z);
                         const float wc = w0 * cs;
                         o[4 * e] = sn;
                         o[4 * e + 1] = wc * w1[h][0];

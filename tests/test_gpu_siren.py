@@ -6,7 +6,7 @@
   pre-rounding values differ from the oracle's by ~1e-6 relative; each BF16 rounding turns
   such a difference into a full ulp (2^-8) with probability ~1e-6 / 2^-8, and the flipped
   values feed 256 sums of the next layer, so the two BF16 computations decorrelate partly
-  over the four layers (measured: about a tenth of the full BF16 noise in RMS, half of it in
+  over the four layers (measured: a tenth to a sixth of the full BF16 noise in RMS, half of it in
   the maximum). Bounds, relative to the outputs' RMS: values 1e-3 RMS and 2e-2 for any single
   element, Jacobian 2e-3 and 3e-2 (its rows pass through one more rounding per layer), and
   1e-4 for the mean difference of any output over all points (a missing or misplaced term

@@ -11,7 +11,7 @@
   the two-fluid parallel field.
 * With the neural field the push is compared with the FP64 oracle running the same network
   (oracle.siren_field, BF16 reading): one short run, increments of R and gamma v_par
-  measured against their own size. The network's BF16 noise (about 3e-4 RMS and 7e-3 at
+  measured against their own size. The network's BF16 noise (about 4e-4 RMS and 7e-3 at
   worst of the field, tests/test_gpu_siren.py) bounds what can agree.
 """
 import numpy as np
