@@ -61,7 +61,8 @@ constexpr int kChunksPerTile = 3 * 8;
 constexpr int kComputeThreads = 512;            // arrivals on each h_ready barrier
 constexpr int kThreads = 576;
 constexpr int kMmaWarp = 16, kTmaWarp = 17;
-constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + kW5Bytes + 1024 + 256;
+constexpr uint32_t kPtsBytes = 16u * 16u * 16u;  // per compute warp: its 16 points as float4
+constexpr size_t kSmemBytes = kHBytes + kStagesW * kChunkBytes + kW5Bytes + kPtsBytes + 1024 + 256;
 
 struct EvalParams {
     const float *P;  // master parameters
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sH = smem;
     uint8_t *sW = smem + kHBytes;
     uint8_t *sW5 = sW + kStagesW * kChunkBytes;  // W5, resident for the whole launch
-    uint64_t *full = (uint64_t *)(sW5 + kW5Bytes);
+    float4 *sPts = (float4 *)(sW5 + kW5Bytes);  // [16 compute warps][16 points]
+    uint64_t *full = (uint64_t *)(sW5 + kW5Bytes + kPtsBytes);
     uint64_t *empty = full + kStagesW;
     uint64_t *h_ready = empty + kStagesW; // [2]: activations of a half written, its accumulator drained
     uint64_t *acc = h_ready + 2;          // [2]: accumulator of a half complete
@@ -363,11 +365,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t *hrow0 = sH + ((lq * 32 + lane) >> 3) * 4096 + (lane & 7) * 128;
         uint8_t *hrow1 = hrow0 + 16 * 4096;
         const uint32_t rsw = (uint32_t)(lane & 7);
-        const unsigned full_mask = 0xffffffffu;
         uint32_t na0 = 0, na1 = 0, no = 0, noa = 0;
         bool ok = true, first = true;
         int64_t base_prev = 0;
-        // this warp's 16 points: lane i < 16 holds point 16 rg + i, shared by shuffles; the
+        // this warp's 16 points: lane i < 16 holds point 16 rg + i and puts it in the warp's
+        // shared-memory slots for the first layer, where every lane reads it by broadcast; the
         // next tile's are fetched while the current one runs
         float px = 0.f, py = 0.f, pz = 0.f;
         const int pt_off = rg * 16 + (lane & 15);
@@ -379,8 +381,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 pz = __ldg(p.in.p + 3 * P + 2) * p.in.x_scale;
             }
         }
+        float4 *wpts = sPts + warp * 16;
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int64_t base = t * kPts;
+            __syncwarp();  // every lane done with the previous tile's points
+            if (lane < 16) wpts[lane] = make_float4(px, py, pz, 0.f);
+            __syncwarp();
             // Layer 1 on the CUDA cores, half 0 then half 1. The previous tile's output layer
             // still runs meanwhile: half 0 overwrites input features 0-127 once the output
             // MMAs over them are done (out_a); before half 0 is announced, the output
@@ -402,8 +408,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int src = 2 * p2 + e;
-                        const float x0 = __shfl_sync(full_mask, px, src), x1 = __shfl_sync(full_mask, py, src),
-                                    x2 = __shfl_sync(full_mask, pz, src);
+                        const float4 xq = wpts[src];
+                        const float x0 = xq.x, x1 = xq.y, x2 = xq.z;
                         const float z = w0 * fmaf(w1[h][0], x0, fmaf(w1[h][1], x1, fmaf(w1[h][2], x2, b1[h])));
                         // the hardware sine and cosine on z directly (|z| reaches tens here, w0
                         // = 30): their error, a few 1e-6 at most there, stays three orders below
